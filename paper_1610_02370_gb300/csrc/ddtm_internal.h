@@ -1,0 +1,140 @@
+// Host-side internals of libddtm: the context, device buffers, geometry and
+// the launch wrappers that the C ABI (api.cu) and the solvers call.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ddtm.h"
+
+namespace ddtm {
+
+// Error carrying a DDTM_ERR_* code; thrown inside the library, turned into a
+// return status at the C boundary.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char* what);
+#define CK(x) ::ddtm::cuda_check((x), #x)
+#define CKL(what) ::ddtm::cuda_check(cudaGetLastError(), what)
+
+// Owned device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() {}
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release();
+  void ensure(size_t n);  // grow to at least n bytes (contents not kept)
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Fine-lattice geometry in the internal block layout (see common.cuh).
+struct FineGeom {
+  int L[4];   // lattice extent per direction mu = t, x, y, z
+  int b[4];   // block extent per direction
+  int NB[4];  // blocks per direction
+  int Vb = 0, Nb = 0;
+  long V = 0;
+  int bc_t = 0;
+  std::vector<uint32_t> h_loc_nbr, h_loc_coord;
+  std::vector<int> h_blk_nbr;
+  DevBuf loc_nbr, loc_coord, blk_nbr;
+  DevBuf colour_blocks;  // [2][Nb/2]: blocks of colour 0 (red), then colour 1 (black)
+};
+
+// One coarse level: a lattice of aggregates with 2*nv dofs per site.
+struct CoarseLevel {
+  int lat[4];        // extent per direction mu
+  int Nc = 0;        // sites
+  int nv = 0, n = 0; // n = 2 nv
+  std::vector<int> h_nbr;      // [8][Nc] neighbour site, hop k = 2 mu + (0 fwd, 1 bwd)
+  std::vector<int> h_even, h_odd;
+  DevBuf nbr, even, odd;       // device copies
+  int prec = 1;                // storage precision of the operator blocks
+  DevBuf Dc;                   // [site][9][col][row] complex, see coarse.cu
+  DevBuf Dinv;                 // inverses of (self + i mu_c Gamma5_c) on even sites
+  double inv_mu = 0;
+  bool inv_valid = false;
+  bool built = false;
+};
+
+struct ScratchPool {
+  std::map<std::string, DevBuf*> bufs;
+  ~ScratchPool();
+  void* get(const std::string& name, size_t bytes);
+};
+
+}  // namespace ddtm
+
+struct ddtm_field {
+  ddtm_ctx* ctx;
+  int prec;
+  int nrhs;
+  size_t stride;  // complex elements per rhs (12 * V)
+  ddtm::DevBuf data;
+  ddtm::DevBuf nrm;  // FP16 only: one float per site and rhs
+};
+
+struct ddtm_ctx {
+  ddtm::FineGeom g;
+  cudaStream_t stream = 0;
+  std::string err;
+  ddtm_params p;
+  bool gauge = false;
+  double kappa = 0, csw = 0;
+  ddtm::DevBuf links[3];   // per precision, internal layout
+  ddtm::DevBuf clover[3];  // per precision, packed site term (incl. m+4)
+  ddtm::DevBuf sinv[3];    // per precision, even-site inverse of site term + i mu gamma5
+  double sinv_mu[3] = {0, 0, 0};
+  bool sinv_ok[3] = {false, false, false};
+  // level-0 aggregation
+  int nv0 = 0;
+  ddtm::DevBuf tv0;        // test vectors: nv0 fine FP32 fields (internal layout)
+  ddtm::DevBuf P0;         // orthonormalised P, FP32: [blk][s][i][6][Vb] complex
+  ddtm::DevBuf P0h;        // FP16 copy of P0
+  ddtm::CoarseLevel c1;
+  bool have_P = false;
+  bool setup_done = false;
+  double setup_mu = 0;
+  double setup_s = 0;
+  ddtm::ScratchPool scratch;
+};
+
+namespace ddtm {
+
+// ---- geometry.cu -------------------------------------------------------------
+void build_geometry(FineGeom& g);
+void build_coarse_geometry(const FineGeom& g, CoarseLevel& c);
+// canonical FP64 complex spinor (one rhs) <-> internal field of precision prec
+void launch_spinor_from_canon(const FineGeom& g, int prec, void* d, float* nrm, const double* in, cudaStream_t s);
+void launch_spinor_to_canon(const FineGeom& g, int prec, const void* d, const float* nrm, double* out, cudaStream_t s);
+// canonical FP64 links -> internal FP64 links
+void launch_links_from_canon(const FineGeom& g, double* out, const double* U, cudaStream_t s);
+// element-wise precision conversion of complex arrays (double2 -> float2 / half2)
+void launch_convert_complex(const double* in, int prec_out, void* out, size_t n, cudaStream_t s);
+// count non-finite doubles
+void launch_count_nonfinite(const double* a, size_t n, int* counter, cudaStream_t s);
+
+// ---- dirac.cu --------------------------------------------------------------------
+void launch_clover_build(const FineGeom& g, double* clov, const double* Ucanon, double m_plus_4, double csw,
+                         cudaStream_t s);
+void launch_site_inverse(const FineGeom& g, int prec, void* out, const double* clov64, double mu, cudaStream_t s);
+void launch_dslash(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
+                   const void* links, const void* clover, double mu, cudaStream_t s);
+
+// ---- sap.cu ----------------------------------------------------------------------
+void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,
+                     const void* clover, const void* sinv, const int* blocks, const int* zero_blocks, int nblocks,
+                     int zero_x, int nmr, double mu, cudaStream_t s);
+
+}  // namespace ddtm
