@@ -118,6 +118,9 @@ const char* ddtm_last_error(ddtm_ctx* ctx);
 int ddtm_set_stream(ddtm_ctx* ctx, void* cuda_stream);
 /* Fill p with the defaults described at ddtm_params. */
 int ddtm_default_params(ddtm_params* p);
+/* Copy the context's current parameters (defaults with block[0] set to the
+ * block of ddtm_create until ddtm_set_params is called) into *p. */
+int ddtm_get_params(ddtm_ctx* ctx, ddtm_params* p);
 /* Validate and store parameters.  Changing block[0] after ddtm_create is
  * rejected (DDTM_ERR_ARG): it fixes the internal layout. */
 int ddtm_set_params(ddtm_ctx* ctx, const ddtm_params* p);

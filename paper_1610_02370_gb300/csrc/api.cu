@@ -186,6 +186,13 @@ int ddtm_set_stream(ddtm_ctx* ctx, void* stream) {
   API_END(ctx)
 }
 
+int ddtm_get_params(ddtm_ctx* ctx, ddtm_params* p) {
+  API_BEGIN(ctx)
+  if (!p) throw Error(DDTM_ERR_ARG, "null params");
+  *p = ctx->p;
+  API_END(ctx)
+}
+
 int ddtm_set_params(ddtm_ctx* ctx, const ddtm_params* p) {
   API_BEGIN(ctx)
   if (!p) throw Error(DDTM_ERR_ARG, "null params");

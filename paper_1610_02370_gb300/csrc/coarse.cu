@@ -1,0 +1,366 @@
+// Coarse operator D_c(mu) = P^dagger D P + i mu Gamma5_c (Sec. 2.3): Galerkin
+// build, stencil, even-odd reduction pieces, and the self-block inverses of
+// the even-odd coarsest solve (Sec. 2.5).
+//
+// Storage: Dc[((x*9 + d)*n + col)*n + row], complex FP32 or FP16, n = 2 nv,
+// d = 0 self (without the twist), d = 1 + k for hop k = 2 mu + (0 fwd, 1 bwd):
+// the block coupling site x to its neighbour in direction +mu (k even) or
+// -mu (k odd).  Column-major blocks make the per-row threads of the stencil
+// read consecutive addresses.  The twist i mu_c Gamma5_c (Gamma5_c = +1 on
+// dofs < nv, -1 above) is added on the fly, so one build serves +mu, -mu and
+// the shifted coarsest twist delta*mu.
+#include "common.cuh"
+#include "ddtm_internal.h"
+#include "coarse.h"
+
+namespace ddtm {
+
+template <typename DS> __device__ __forceinline__ cplx<float> ldD(const DS* p);
+template <> __device__ __forceinline__ cplx<float> ldD<float2>(const float2* p) { return ld(p); }
+template <> __device__ __forceinline__ cplx<float> ldD<__half2>(const __half2* p) { return ld(p); }
+template <typename DS> __device__ __forceinline__ void stD(DS* p, cplx<float> v);
+template <> __device__ __forceinline__ void stD<float2>(float2* p, cplx<float> v) { st(p, v); }
+template <> __device__ __forceinline__ void stD<__half2>(__half2* p, cplx<float> v) { st(p, v); }
+
+__device__ __forceinline__ size_t pix(int blk, int s, int i, int comp, int loc, int nv, int Vb) {
+  return (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc;
+}
+
+// ---- Galerkin build ----------------------------------------------------------------
+// One CTA per aggregate A, thread = site.  For every column (s', j) of P:
+//   y0(x)  = S phi(x) + hops of phi that stay inside A          (self part)
+//   yk(x)  = hop k of phi read in the neighbour aggregate, for x on face k
+// with phi = column (s', j) of every aggregate; then
+//   Dc[A][0][col][row]   = sum_{x in A} <P_row(x), y0(x)>
+//   Dc[A][1+k][col][row] = sum_{x on face k} <P_row(x), yk(x)>
+// Face k of a block = sites whose hop k leaves the block; faces are stored
+// compactly (face_list / face_idx tables, offsets face_off).
+struct FaceTables {
+  const int* idx;   // [8][Vb]: slot of site in face k or -1
+  const int* list;  // [face_off[8]]: site of each slot
+  int off[9];
+};
+
+template <typename DS>
+__global__ void k_galerkin(DS* __restrict__ Dc, const float2* __restrict__ P, Links<PREC_F32> U, Clover<PREC_F32> C,
+                           Geo g, FaceTables f, int nv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Vb = g.Vb;
+  cplx<float>* y0 = reinterpret_cast<cplx<float>*>(smem_raw);  // [12][Vb]
+  cplx<float>* yf = y0 + 12 * Vb;                                // [12][face slots]
+  const int nf = f.off[8];
+  const int A = blockIdx.x;
+  const int n = 2 * nv;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int col = 0; col < n; col++) {
+    const int sp = col / nv, j = col - sp * nv;
+    for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
+      cplx<float> phi[12], acc[12], out[12];
+#pragma unroll
+      for (int c = 0; c < 12; c++) { phi[c] = cplx<float>(0, 0); acc[c] = cplx<float>(0, 0); }
+      for (int comp = 0; comp < 6; comp++) phi[6 * sp + comp] = ld(P + pix(A, sp, j, comp, loc, nv, Vb));
+      C.apply(A, loc, phi, out);
+      for (int k = 0; k < 8; k++) {
+        const int mu = k >> 1;
+        const bool fwd = (k & 1) == 0;
+        Nbr nb = neighbour(g, A, loc, k);
+        cplx<float> p[12], h[6], wv[6], u[9];
+#pragma unroll
+        for (int c = 0; c < 12; c++) p[c] = cplx<float>(0, 0);
+        for (int comp = 0; comp < 6; comp++) p[6 * sp + comp] = ld(P + pix(nb.blk, sp, j, comp, nb.loc, nv, Vb));
+        project<float>(mu, fwd, p, h);
+        if (fwd) { U.load(A, loc, mu, u); mul_U<float>(u, h, wv); }
+        else { U.load(nb.blk, nb.loc, mu, u); mul_Udag<float>(u, h, wv); }
+        if (nb.flip)
+          for (int q = 0; q < 6; q++) wv[q] = -wv[q];
+        if (!nb.cross) {
+          reconstruct<float>(mu, fwd, wv, acc);
+        } else {
+          cplx<float> part[12];
+#pragma unroll
+          for (int c = 0; c < 12; c++) part[c] = cplx<float>(0, 0);
+          reconstruct<float>(mu, fwd, wv, part);
+          int slot = f.off[k] + f.idx[k * Vb + loc];
+#pragma unroll
+          for (int c = 0; c < 12; c++) yf[c * nf + slot] = -0.5f * part[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 12; c++) y0[c * Vb + loc] = out[c] + (-0.5f) * acc[c];
+    }
+    __syncthreads();
+    for (int o = w; o < 9 * n; o += nw) {
+      const int d = o / n, row = o - d * n;
+      const int s = row / nv, i = row - s * nv;
+      cplx<float> acc(0, 0);
+      if (d == 0) {
+        for (int comp = 0; comp < 6; comp++)
+          for (int loc = lane; loc < Vb; loc += 32)
+            cmac_conj(acc, ld(P + pix(A, s, i, comp, loc, nv, Vb)), y0[(6 * s + comp) * Vb + loc]);
+      } else {
+        const int k = d - 1;
+        for (int comp = 0; comp < 6; comp++)
+          for (int q = f.off[k] + lane; q < f.off[k + 1]; q += 32)
+            cmac_conj(acc, ld(P + pix(A, s, i, comp, f.list[q], nv, Vb)), yf[(6 * s + comp) * nf + q]);
+      }
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+      if (lane == 0) stD(Dc + (((size_t)A * 9 + d) * n + col) * n + row, acc);
+    }
+    __syncthreads();
+  }
+}
+
+void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* Dc, const float2* P, const void* links32,
+                     const void* clover32, int nv, cudaStream_t st) {
+  Geo q{g.Vb, g.Nb, g.loc_nbr.as<uint32_t>(), g.blk_nbr.as<int>()};
+  FaceTables f;
+  f.idx = faces.idx.as<int>();
+  f.list = faces.list.as<int>();
+  for (int k = 0; k < 9; k++) f.off[k] = faces.off[k];
+  size_t smem = (size_t)12 * (g.Vb + faces.off[8]) * sizeof(cplx<float>);
+  int threads = g.Vb >= 256 ? 256 : ((g.Vb + 31) / 32) * 32;
+  Links<PREC_F32> U{(const float2*)links32, g.Vb};
+  Clover<PREC_F32> C{(const float2*)clover32, g.Vb};
+  if (dprec == PREC_F16) {
+    CK(cudaFuncSetAttribute(k_galerkin<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_galerkin<__half2><<<g.Nb, threads, smem, st>>>((__half2*)Dc, P, U, C, q, f, nv);
+  } else {
+    CK(cudaFuncSetAttribute(k_galerkin<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_galerkin<float2><<<g.Nb, threads, smem, st>>>((float2*)Dc, P, U, C, q, f, nv);
+  }
+  CKL("galerkin");
+}
+
+void build_faces(const FineGeom& g, FaceDev& faces) {
+  std::vector<int> idx(8 * g.Vb, -1), list;
+  for (int k = 0; k < 8; k++) {
+    faces.off[k] = (int)list.size();
+    for (int loc = 0; loc < g.Vb; loc++)
+      if ((g.h_loc_nbr[k * g.Vb + loc] >> 16) & 1) {
+        idx[k * g.Vb + loc] = (int)list.size() - faces.off[k];
+        list.push_back(loc);
+      }
+  }
+  faces.off[8] = (int)list.size();
+  faces.idx.ensure(idx.size() * 4);
+  faces.list.ensure(list.size() * 4 + 4);
+  CK(cudaMemcpy(faces.idx.p, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(faces.list.p, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
+}
+
+// ---- coarse stencil ---------------------------------------------------------------
+// Threads: n per site, SPB sites per CTA; thread (q, r) computes row r of
+// output slot idx = blockIdx.x * SPB + q, whose lattice site is osite[idx]
+// (idx itself when osite == nullptr).  The self term reads x_self[idx], the
+// hop d reads x_hop[tab[(d-1) * nout + idx]]; with full-lattice vectors
+// osite = nullptr and tab = the full neighbour table, with parity-compact
+// vectors tab maps into the compact vector of the other parity.
+//   mode & 1: self block + twist i mu_c Gamma5_c;  mode & 2: the 8 hops
+//   y[idx] = sy * y[idx] + sres * result   (sy = 0 overwrites)
+template <typename DS>
+__global__ void k_coarse_apply(cplx<float>* __restrict__ y, const cplx<float>* __restrict__ x_self,
+                               const cplx<float>* __restrict__ x_hop, const DS* __restrict__ Dc, const int* __restrict__ tab,
+                               const int* __restrict__ osite, int nout, int n, int nv, float mu_c, int mode, float sres,
+                               float sy) {
+  const int spb = blockDim.x / n;
+  const int q = threadIdx.x / n, r = threadIdx.x - q * n;
+  const int idx = blockIdx.x * spb + q;
+  if (q >= spb || idx >= nout) return;
+  const int site = osite ? osite[idx] : idx;
+  cplx<float> acc(0, 0);
+  if (mode & 1) {
+    const DS* A = Dc + (size_t)site * 9 * n * n + r;
+    const cplx<float>* v = x_self + (size_t)idx * n;
+#pragma unroll 4
+    for (int k = 0; k < n; k++) cmac(acc, ldD<DS>(A + (size_t)k * n), v[k]);
+    float m = r < nv ? mu_c : -mu_c;
+    acc = acc + m * times_i(v[r]);
+  }
+  if (mode & 2)
+    for (int d = 1; d < 9; d++) {
+      const int src = __ldg(tab + (size_t)(d - 1) * nout + idx);
+      const DS* A = Dc + ((size_t)site * 9 + d) * n * n + r;
+      const cplx<float>* v = x_hop + (size_t)src * n;
+#pragma unroll 4
+      for (int k = 0; k < n; k++) cmac(acc, ldD<DS>(A + (size_t)k * n), v[k]);
+    }
+  size_t o = (size_t)idx * n + r;
+  cplx<float> res = sres * acc;
+  y[o] = sy == 0.f ? res : sy * y[o] + res;
+}
+
+// t[e] = Dinv_e (sr * rhs[e] + sh * hops(v)) on the even sites (compact even
+// output, v compact odd); rhs or v may be null.  Hop and inverse are fused.
+template <typename DS>
+__global__ void k_coarse_even(cplx<float>* __restrict__ t, const cplx<float>* __restrict__ rhs, const cplx<float>* __restrict__ v,
+                              const DS* __restrict__ Dc, const float2* __restrict__ Dinv, const int* __restrict__ tab,
+                              const int* __restrict__ even, int ne, int n, float sr, float sh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int spb = blockDim.x / n;
+  cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem_raw);
+  const int q = threadIdx.x / n, r = threadIdx.x - q * n;
+  const int e = blockIdx.x * spb + q;
+  const bool act = q < spb && e < ne;
+  if (act) {
+    const int site = even[e];
+    cplx<float> acc(0, 0);
+    if (v)
+      for (int d = 1; d < 9; d++) {
+        const int src = __ldg(tab + (size_t)(d - 1) * ne + e);
+        const DS* A = Dc + ((size_t)site * 9 + d) * n * n + r;
+        const cplx<float>* vv = v + (size_t)src * n;
+#pragma unroll 4
+        for (int k = 0; k < n; k++) cmac(acc, ldD<DS>(A + (size_t)k * n), vv[k]);
+      }
+    acc = sh * acc;
+    if (rhs) acc = acc + sr * rhs[(size_t)e * n + r];
+    hs[q * n + r] = acc;
+  }
+  __syncthreads();
+  if (act) {
+    cplx<float> out(0, 0);
+    const float2* Mi = Dinv + (size_t)e * n * n + r;
+#pragma unroll 4
+    for (int k = 0; k < n; k++) cmac(out, ld(Mi + (size_t)k * n), hs[q * n + k]);
+    t[(size_t)e * n + r] = out;
+  }
+}
+
+// gather (dir = 0: compact[i] = full[list[i]]) or scatter (dir = 1)
+__global__ void k_parity_copy(cplx<float>* __restrict__ compact, cplx<float>* __restrict__ full, const int* __restrict__ list,
+                              int cnt, int n, int dir) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)cnt * n) return;
+  int i = (int)(t / n), r = (int)(t - (size_t)i * n);
+  size_t f = (size_t)list[i] * n + r;
+  if (dir == 0) compact[t] = full[f];
+  else full[f] = compact[t];
+}
+
+// Inverse of (self block + i mu_c Gamma5_c) per even site by Gauss-Jordan
+// elimination with partial pivoting in FP64; one CTA per site, thread = row.
+template <typename DS>
+__global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__ Dc, const int* __restrict__ even, int n,
+                               int nv, double mu_c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<double>* M = reinterpret_cast<cplx<double>*>(smem_raw);  // [n][2n] row-major augmented
+  __shared__ int piv;
+  const int e = blockIdx.x, site = even[e];
+  const int r = threadIdx.x;
+  const int w2 = 2 * n;
+  if (r < n) {
+    for (int c = 0; c < n; c++) {
+      cplx<float> a = ldD<DS>(Dc + ((size_t)site * 9 * n + c) * n + r);  // d = 0, column c, row r
+      M[r * w2 + c] = cplx<double>(a.re, a.im);
+      M[r * w2 + n + c] = cplx<double>(r == c ? 1.0 : 0.0, 0.0);
+    }
+    M[r * w2 + r].im += r < nv ? mu_c : -mu_c;
+  }
+  __syncthreads();
+  for (int c = 0; c < n; c++) {
+    if (r == 0) {
+      int p = c;
+      double best = norm2(M[c * w2 + c]);
+      for (int k = c + 1; k < n; k++)
+        if (norm2(M[k * w2 + c]) > best) { best = norm2(M[k * w2 + c]); p = k; }
+      piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != c && r < w2) {  // swap rows c and p, column r (and r + n) per thread
+      for (int cc = r; cc < w2; cc += blockDim.x) {
+        cplx<double> tmp = M[c * w2 + cc];
+        M[c * w2 + cc] = M[p * w2 + cc];
+        M[p * w2 + cc] = tmp;
+      }
+    }
+    __syncthreads();
+    cplx<double> d = M[c * w2 + c];
+    double dn = norm2(d);
+    cplx<double> inv(d.re / dn, -d.im / dn);
+    __syncthreads();
+    for (int cc = r; cc < w2; cc += blockDim.x) M[c * w2 + cc] = M[c * w2 + cc] * inv;
+    __syncthreads();
+    if (r < n && r != c) {
+      cplx<double> fct = M[r * w2 + c];
+      for (int cc = 0; cc < w2; cc++) M[r * w2 + cc] = M[r * w2 + cc] - fct * M[c * w2 + cc];
+    }
+    __syncthreads();
+  }
+  if (r < n)
+    for (int c = 0; c < n; c++) {
+      cplx<double> v = M[r * w2 + n + c];
+      Dinv[((size_t)e * n + c) * n + r] = make_float2((float)v.re, (float)v.im);  // column-major
+    }
+}
+
+static int spb_for(int n) { return n >= 128 ? 1 : (n >= 64 ? 2 : 4); }
+
+template <typename DS>
+static void coarse_apply_t(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
+                           const int* osite, int nout, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
+  int spb = spb_for(c.n);
+  unsigned grid = (unsigned)((nout + spb - 1) / spb);
+  if (grid == 0) return;
+  k_coarse_apply<DS><<<grid, spb * c.n, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, (float)mu_c, mode,
+                                                 sres, sy);
+  CKL("coarse_apply");
+}
+
+void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, double mu_c, int mode, float sres,
+                              float sy, cudaStream_t st) {
+  if (c.prec == PREC_F16) coarse_apply_t<__half2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, mu_c, mode, sres, sy, st);
+  else coarse_apply_t<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, mu_c, mode, sres, sy, st);
+}
+
+void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e,
+                             double mu_c, int mode, float sres, float sy, cudaStream_t st) {
+  int no = (int)c.h_odd.size();
+  if (c.prec == PREC_F16)
+    coarse_apply_t<__half2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, mu_c, mode, sres, sy, st);
+  else
+    coarse_apply_t<float2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, mu_c, mode, sres, sy, st);
+}
+
+void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, float sr,
+                        float sh, cudaStream_t st) {
+  int spb = spb_for(c.n);
+  int ne = (int)c.h_even.size();
+  unsigned grid = (unsigned)((ne + spb - 1) / spb);
+  size_t smem = (size_t)spb * c.n * sizeof(cplx<float>);
+  if (c.prec == PREC_F16)
+    k_coarse_even<__half2><<<grid, spb * c.n, smem, st>>>(t, rhs, v, c.Dc.as<__half2>(), c.Dinv.as<float2>(),
+                                                          c.nbr_eo.as<int>(), c.even.as<int>(), ne, c.n, sr, sh);
+  else
+    k_coarse_even<float2><<<grid, spb * c.n, smem, st>>>(t, rhs, v, c.Dc.as<float2>(), c.Dinv.as<float2>(),
+                                                         c.nbr_eo.as<int>(), c.even.as<int>(), ne, c.n, sr, sh);
+  CKL("coarse_even");
+}
+
+void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int dir, cudaStream_t st) {
+  int cnt = parity == 0 ? (int)c.h_even.size() : (int)c.h_odd.size();
+  const int* list = parity == 0 ? c.even.as<int>() : c.odd.as<int>();
+  size_t tot = (size_t)cnt * c.n;
+  k_parity_copy<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(compact, full, list, cnt, c.n, dir);
+  CKL("parity_copy");
+}
+
+void launch_self_inverse(CoarseLevel& c, double mu_c, cudaStream_t st) {
+  int ne = (int)c.h_even.size();
+  c.Dinv.ensure((size_t)ne * c.n * c.n * sizeof(float2));
+  size_t smem = (size_t)c.n * 2 * c.n * sizeof(cplx<double>);
+  int threads = ((c.n + 31) / 32) * 32;
+  if (c.prec == PREC_F16) {
+    CK(cudaFuncSetAttribute(k_self_inverse<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_self_inverse<__half2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<__half2>(), c.even.as<int>(), c.n, c.nv, mu_c);
+  } else {
+    CK(cudaFuncSetAttribute(k_self_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_self_inverse<float2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(), c.n, c.nv, mu_c);
+  }
+  CKL("self_inverse");
+  c.inv_mu = mu_c;
+  c.inv_valid = true;
+}
+
+}  // namespace ddtm

@@ -59,13 +59,22 @@ struct CoarseLevel {
   int nv = 0, n = 0; // n = 2 nv
   std::vector<int> h_nbr;      // [8][Nc] neighbour site, hop k = 2 mu + (0 fwd, 1 bwd)
   std::vector<int> h_even, h_odd;
-  DevBuf nbr, even, odd;       // device copies
+  // parity-compact neighbour tables: [8][No] even-list index of the neighbour
+  // of odd site i, and [8][Ne] odd-list index of the neighbour of even site i
+  std::vector<int> h_nbr_oe, h_nbr_eo;
+  DevBuf nbr, even, odd, nbr_oe, nbr_eo;  // device copies
   int prec = 1;                // storage precision of the operator blocks
   DevBuf Dc;                   // [site][9][col][row] complex, see coarse.cu
   DevBuf Dinv;                 // inverses of (self + i mu_c Gamma5_c) on even sites
   double inv_mu = 0;
   bool inv_valid = false;
   bool built = false;
+};
+
+// faces of a block: for hop k, the sites whose hop leaves the block
+struct FaceDev {
+  DevBuf idx, list;
+  int off[9] = {0};
 };
 
 struct ScratchPool {
@@ -102,7 +111,11 @@ struct ddtm_ctx {
   ddtm::DevBuf tv0;        // test vectors: nv0 fine FP32 fields (internal layout)
   ddtm::DevBuf P0;         // orthonormalised P, FP32: [blk][s][i][6][Vb] complex
   ddtm::DevBuf P0h;        // FP16 copy of P0
+  ddtm::FaceDev faces;
+  bool faces_ready = false;
   ddtm::CoarseLevel c1;
+  bool c1_geom = false;
+  long coarse_iters = 0;   // accumulated by the coarsest solves
   bool have_P = false;
   bool setup_done = false;
   double setup_mu = 0;

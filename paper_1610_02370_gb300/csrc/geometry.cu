@@ -163,6 +163,20 @@ void build_coarse_geometry(const FineGeom& g, CoarseLevel& c) {
       c.h_nbr[k * c.Nc + i] = canon_index(c.lat, n);
     }
   }
+  std::vector<int> pos(c.Nc);
+  for (size_t i = 0; i < c.h_even.size(); i++) pos[c.h_even[i]] = (int)i;
+  for (size_t i = 0; i < c.h_odd.size(); i++) pos[c.h_odd[i]] = (int)i;
+  int ne = (int)c.h_even.size(), no = (int)c.h_odd.size();
+  c.h_nbr_oe.assign(8 * (size_t)no, 0);
+  c.h_nbr_eo.assign(8 * (size_t)ne, 0);
+  for (int k = 0; k < 8; k++) {
+    for (int i = 0; i < no; i++) c.h_nbr_oe[(size_t)k * no + i] = pos[c.h_nbr[(size_t)k * c.Nc + c.h_odd[i]]];
+    for (int i = 0; i < ne; i++) c.h_nbr_eo[(size_t)k * ne + i] = pos[c.h_nbr[(size_t)k * c.Nc + c.h_even[i]]];
+  }
+  c.nbr_oe.ensure(c.h_nbr_oe.size() * 4 + 4);
+  c.nbr_eo.ensure(c.h_nbr_eo.size() * 4 + 4);
+  CK(cudaMemcpy(c.nbr_oe.p, c.h_nbr_oe.data(), c.h_nbr_oe.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c.nbr_eo.p, c.h_nbr_eo.data(), c.h_nbr_eo.size() * 4, cudaMemcpyHostToDevice));
   c.nbr.ensure(c.h_nbr.size() * 4);
   c.even.ensure(c.h_even.size() * 4 + 4);
   c.odd.ensure(c.h_odd.size() * 4 + 4);

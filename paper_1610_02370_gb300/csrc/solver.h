@@ -23,7 +23,7 @@ void dslash_field(ddtm_ctx* c, ddtm_field* y, const ddtm_field* x, double mu);
 // ncycles red-black SAP cycles on D(mu) x = b from x = 0 (fields of one rhs,
 // precision prec); x and b are internal-layout device pointers.
 void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const float* bn, double mu, int ncycles,
-             int nmr);
+             int nmr, bool from_zero);
 
 void validate_params(ddtm_ctx* c, const ddtm_params& p);
 void invalidate_setup(ddtm_ctx* c);

@@ -1,0 +1,277 @@
+// Gamma5-compatible aggregation (Sec. 2.3): building P from test vectors,
+// restriction R = P^dagger and prolongation P.
+//
+// P layout (FP32 or FP16 complex): P[((blk*2 + s)*nv + i)*6*Vb + comp*Vb + loc]
+// = column (blk, s, i) of P at site loc, spinor component 6 s + comp (spins
+// 2s, 2s+1 x 3 colours), i.e. the chirality-s half of aggregate blk.
+// Coarse vectors: complex FP32 [site][2 nv], dof s*nv + i.
+#include "common.cuh"
+#include "ddtm_internal.h"
+
+namespace ddtm {
+
+__device__ __forceinline__ size_t pidx(int blk, int s, int i, int comp, int loc, int nv, int Vb) {
+  return (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc;
+}
+
+// CTA-wide sum of two doubles, result broadcast (blockDim multiple of 32)
+__device__ __forceinline__ void cta_sum2d(double& a, double& b, double* red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
+  __syncthreads();
+  a = b = 0;
+  for (int k = 0; k < nw; k++) { a += red[2 * k]; b += red[2 * k + 1]; }
+}
+
+// Gather the chirality-s halves of nv test vectors (FP32 fine fields, internal
+// layout, field stride 12*V) into P and orthonormalise each aggregate half by
+// modified Gram-Schmidt in index order, twice; inner products in FP64.
+// One CTA per (blk, s); thread = site loc.
+__global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv, int nv, int Vb, long V) {
+  __shared__ double red[64];
+  const int blk = blockIdx.x >> 1, s = blockIdx.x & 1;
+  const int loc = threadIdx.x;
+  const bool act = loc < Vb;
+  if (act)
+    for (int i = 0; i < nv; i++)
+      for (int comp = 0; comp < 6; comp++)
+        P[pidx(blk, s, i, comp, loc, nv, Vb)] =
+            tv[(size_t)i * 12 * V + ((size_t)blk * 12 + 6 * s + comp) * Vb + loc];
+  __syncthreads();
+  for (int sweep = 0; sweep < 2; sweep++) {
+    for (int i = 0; i < nv; i++) {
+      double2 vi[6];
+      if (act)
+        for (int comp = 0; comp < 6; comp++) {
+          float2 a = P[pidx(blk, s, i, comp, loc, nv, Vb)];
+          vi[comp] = make_double2(a.x, a.y);
+        }
+      for (int j = 0; j < i; j++) {
+        double re = 0, im = 0;
+        double2 vj[6];
+        if (act)
+          for (int comp = 0; comp < 6; comp++) {
+            float2 a = P[pidx(blk, s, j, comp, loc, nv, Vb)];
+            vj[comp] = make_double2(a.x, a.y);
+            re += vj[comp].x * vi[comp].x + vj[comp].y * vi[comp].y;  // <v_j, v_i>
+            im += vj[comp].x * vi[comp].y - vj[comp].y * vi[comp].x;
+          }
+        cta_sum2d(re, im, red);
+        if (act)
+          for (int comp = 0; comp < 6; comp++) {
+            vi[comp].x -= re * vj[comp].x - im * vj[comp].y;
+            vi[comp].y -= re * vj[comp].y + im * vj[comp].x;
+          }
+      }
+      double nn = 0, dummy = 0;
+      if (act)
+        for (int comp = 0; comp < 6; comp++) nn += vi[comp].x * vi[comp].x + vi[comp].y * vi[comp].y;
+      cta_sum2d(nn, dummy, red);
+      double inv = nn > 0 ? 1.0 / sqrt(nn) : 0.0;
+      if (act)
+        for (int comp = 0; comp < 6; comp++)
+          P[pidx(blk, s, i, comp, loc, nv, Vb)] = make_float2((float)(vi[comp].x * inv), (float)(vi[comp].y * inv));
+      __syncthreads();
+    }
+  }
+}
+
+void launch_build_P(const FineGeom& g, float2* P, const float2* tv, int nv, cudaStream_t st) {
+  int threads = ((g.Vb + 31) / 32) * 32;
+  k_build_P<<<g.Nb * 2, threads, 0, st>>>(P, tv, nv, g.Vb, g.V);
+  CKL("build_P");
+}
+
+template <typename PS>
+__device__ __forceinline__ cplx<float> ldp(const PS* p);
+template <>
+__device__ __forceinline__ cplx<float> ldp<float2>(const float2* p) { return ld(p); }
+template <>
+__device__ __forceinline__ cplx<float> ldp<__half2>(const __half2* p) { return ld(p); }
+
+// c = P^dagger psi per aggregate.  One CTA per block: psi_B staged in shared
+// memory (FP32, [12][Vb]); warp w computes outputs o = w, w + nwarps, ...,
+// lanes striding over sites, then a warp reduction.
+template <int PI, typename PS>
+__global__ void k_restrict(cplx<float>* __restrict__ c, Spinor<PI> psi, const PS* __restrict__ P, int nv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<float>* sp = reinterpret_cast<cplx<float>*>(smem_raw);
+  const int Vb = psi.Vb;
+  const int blk = blockIdx.x;
+  for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
+    cplx<typename Prec<PI>::real> v[12];
+    psi.load(blk, loc, v);
+#pragma unroll
+    for (int k = 0; k < 12; k++) sp[k * Vb + loc] = cplx<float>((float)v[k].re, (float)v[k].im);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = 2 * nv;
+  for (int o = w; o < n; o += nw) {
+    int s = o / nv, i = o - s * nv;
+    cplx<float> acc(0, 0);
+    const PS* col = P + ((size_t)(blk * 2 + s) * nv + i) * 6 * Vb;
+    for (int comp = 0; comp < 6; comp++)
+      for (int loc = lane; loc < Vb; loc += 32) cmac_conj(acc, ldp<PS>(col + comp * Vb + loc), sp[(6 * s + comp) * Vb + loc]);
+    acc.re = warp_sum(acc.re);
+    acc.im = warp_sum(acc.im);
+    if (lane == 0) c[(size_t)blk * n + o] = acc;
+  }
+}
+
+// x = P e (mode 0) or x += P e (mode 1).  One CTA per block, thread = site;
+// e_B staged in shared memory.
+template <int PO, typename PS>
+__global__ void k_prolong(Spinor<PO> x, const cplx<float>* __restrict__ e, const PS* __restrict__ P, int nv, int add) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<float>* se = reinterpret_cast<cplx<float>*>(smem_raw);
+  const int Vb = x.Vb;
+  const int blk = blockIdx.x;
+  const int n = 2 * nv;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) se[k] = e[(size_t)blk * n + k];
+  __syncthreads();
+  for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
+    typedef typename Prec<PO>::real R;
+    cplx<R> out[12];
+    if (add) x.loadw(blk, loc, out);
+    for (int s = 0; s < 2; s++)
+      for (int comp = 0; comp < 6; comp++) {
+        cplx<float> acc(0, 0);
+        for (int i = 0; i < nv; i++)
+          cmac(acc, ldp<PS>(P + (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc), se[s * nv + i]);
+        cplx<R> a((R)acc.re, (R)acc.im);
+        out[6 * s + comp] = add ? out[6 * s + comp] + a : a;
+      }
+    x.store(blk, loc, out);
+  }
+}
+
+template <typename PS>
+static void restrict_t(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const PS* P, int nv,
+                       cudaStream_t st) {
+  size_t smem = (size_t)12 * g.Vb * sizeof(cplx<float>);
+  int threads = 256;
+  if (pin == PREC_F64) {
+    static bool cfg = false;
+    if (!cfg) { CK(cudaFuncSetAttribute(k_restrict<PREC_F64, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000)); cfg = true; }
+    k_restrict<PREC_F64, PS><<<g.Nb, threads, smem, st>>>(c, Spinor<PREC_F64>{(double2*)psi, nullptr, g.Vb}, P, nv);
+  } else if (pin == PREC_F32) {
+    static bool cfg = false;
+    if (!cfg) { CK(cudaFuncSetAttribute(k_restrict<PREC_F32, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000)); cfg = true; }
+    k_restrict<PREC_F32, PS><<<g.Nb, threads, smem, st>>>(c, Spinor<PREC_F32>{(float2*)psi, nullptr, g.Vb}, P, nv);
+  } else {
+    static bool cfg = false;
+    if (!cfg) { CK(cudaFuncSetAttribute(k_restrict<PREC_F16, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000)); cfg = true; }
+    k_restrict<PREC_F16, PS><<<g.Nb, threads, smem, st>>>(c, Spinor<PREC_F16>{(__half2*)psi, (float*)pn, g.Vb}, P, nv);
+  }
+  CKL("restrict");
+}
+
+template <typename PS>
+static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const PS* P, int nv, int add,
+                      cudaStream_t st) {
+  size_t smem = (size_t)2 * nv * sizeof(cplx<float>);
+  int threads = g.Vb < 128 ? ((g.Vb + 31) / 32) * 32 : 128;
+  if (pout == PREC_F64)
+    k_prolong<PREC_F64, PS><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F64>{(double2*)x, nullptr, g.Vb}, e, P, nv, add);
+  else if (pout == PREC_F32)
+    k_prolong<PREC_F32, PS><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F32>{(float2*)x, nullptr, g.Vb}, e, P, nv, add);
+  else
+    k_prolong<PREC_F16, PS><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F16>{(__half2*)x, xn, g.Vb}, e, P, nv, add);
+  CKL("prolong");
+}
+
+void launch_restrict(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const void* P,
+                     int pprec, int nv, cudaStream_t st) {
+  if (pprec == PREC_F16) restrict_t<__half2>(g, pin, c, psi, pn, (const __half2*)P, nv, st);
+  else restrict_t<float2>(g, pin, c, psi, pn, (const float2*)P, nv, st);
+}
+
+void launch_prolong(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const void* P, int pprec,
+                    int nv, int add, cudaStream_t st) {
+  if (pprec == PREC_F16) prolong_t<__half2>(g, pout, x, xn, e, (const __half2*)P, nv, add, st);
+  else prolong_t<float2>(g, pout, x, xn, e, (const float2*)P, nv, add, st);
+}
+
+__global__ void k_P_to_half(const float2* __restrict__ P, __half2* __restrict__ Ph, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { float2 a = P[i]; Ph[i] = __floats2half2_rn(a.x, a.y); }
+}
+
+void launch_P_to_half(const float2* P, __half2* Ph, size_t n, cudaStream_t st) {
+  k_P_to_half<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, Ph, n);
+  CKL("P_to_half");
+}
+
+// Counter-based Gaussian draws for the random start of the setup: element i
+// takes two SplitMix64 outputs (Steele, Lea, Flood 2014) of key + 2i and
+// key + 2i + 1 as uniforms and maps them by Box-Muller to (re, im) ~ N(0, 1).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_gaussian(float2* __restrict__ out, size_t n, uint64_t key) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double u1 = ((splitmix64(key + 2 * i) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  double u2 = ((splitmix64(key + 2 * i + 1) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  double r = sqrt(-2.0 * log(u1)), th = 6.283185307179586 * u2;
+  out[i] = make_float2((float)(r * cos(th)), (float)(r * sin(th)));
+}
+
+void launch_gaussian(float2* out, size_t n, uint64_t key, cudaStream_t st) {
+  k_gaussian<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, key);
+  CKL("gaussian");
+}
+
+// P in canonical form for inspection: W[(s*nv + i)][site][spin][colour], zero
+// on the other chirality.
+struct CanonMapT {
+  int L[4], b[4], NB[4];
+  int Vb, Nb;
+  const uint32_t* loc_coord;
+};
+
+__global__ void k_P_to_canon(double2* __restrict__ W, const float2* __restrict__ P, int nv, CanonMapT m) {
+  long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long V = (long)m.Vb * m.Nb;
+  if (s >= V) return;
+  int blk = (int)(s / m.Vb), loc = (int)(s - (long)blk * m.Vb);
+  int B[4], r = blk;
+  B[1] = r % m.NB[1]; r /= m.NB[1];
+  B[2] = r % m.NB[2]; r /= m.NB[2];
+  B[3] = r % m.NB[3];
+  B[0] = r / m.NB[3];
+  uint32_t lc = m.loc_coord[loc];
+  int t = B[0] * m.b[0] + (lc & 255), x = B[1] * m.b[1] + ((lc >> 8) & 255);
+  int y = B[2] * m.b[2] + ((lc >> 16) & 255), z = B[3] * m.b[3] + ((lc >> 24) & 255);
+  size_t site = (((size_t)t * m.L[3] + z) * m.L[2] + y) * m.L[1] + x;
+  for (int sc = 0; sc < 2; sc++)
+    for (int i = 0; i < nv; i++)
+      for (int c = 0; c < 12; c++) {
+        double2 v = make_double2(0, 0);
+        if (c / 6 == sc) {
+          float2 a = P[pidx(blk, sc, i, c - 6 * sc, loc, nv, m.Vb)];
+          v = make_double2(a.x, a.y);
+        }
+        W[((size_t)(sc * nv + i) * V + site) * 12 + c] = v;
+      }
+}
+
+void launch_P_to_canon(const FineGeom& g, double* W, const float2* P, int nv, cudaStream_t st) {
+  CanonMapT m;
+  for (int k = 0; k < 4; k++) { m.L[k] = g.L[k]; m.b[k] = g.b[k]; m.NB[k] = g.NB[k]; }
+  m.Vb = g.Vb;
+  m.Nb = g.Nb;
+  m.loc_coord = g.loc_coord.as<uint32_t>();
+  k_P_to_canon<<<(unsigned)((g.V + 127) / 128), 128, 0, st>>>((double2*)W, P, nv, m);
+  CKL("P_to_canon");
+}
+
+}  // namespace ddtm

@@ -53,6 +53,7 @@ SIGNATURES = {
     "ddtm_last_error": (ctypes.c_char_p, [_P]),
     "ddtm_set_stream": (_I, [_P, _P]),
     "ddtm_default_params": (_I, [ctypes.POINTER(ddtm_params)]),
+    "ddtm_get_params": (_I, [_P, ctypes.POINTER(ddtm_params)]),
     "ddtm_set_params": (_I, [_P, ctypes.POINTER(ddtm_params)]),
     "ddtm_load_gauge": (_I, [_P, _P, _I, _D, _D]),
     "ddtm_apply_D": (_I, [_P, _P, _P, _I, _D, _I, _I]),
@@ -145,6 +146,12 @@ def ddtm_last_error(ctx):
 
 def ddtm_set_stream(ctx, stream_handle):
     _check(ctx, _lib.ddtm_set_stream(ctx, _P(stream_handle)))
+
+
+def ddtm_get_params(ctx):
+    p = ddtm_params()
+    _check(ctx, _lib.ddtm_get_params(ctx, ctypes.byref(p)))
+    return p
 
 
 def ddtm_set_params(ctx, p):
