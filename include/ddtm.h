@@ -208,6 +208,18 @@ int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, i
 int ddtm_save_setup(ddtm_ctx* ctx, const char* path);
 int ddtm_load_setup(ddtm_ctx* ctx, const char* path);
 
+/* ---- measurement ------------------------------------------------------------ */
+
+/* Per-kernel CUDA-event timing (the paper reports its cost in setup and
+ * solve time, Tables 2-4; these timers break the GPU time down by kernel).
+ * When enabled, every kernel launch of the library is bracketed by two events
+ * on its stream.  Timers are process-wide (shared by all contexts). */
+int ddtm_timer_enable(ddtm_ctx* ctx, int on);
+int ddtm_timer_reset(ddtm_ctx* ctx);
+/* Write a JSON object {"kernel": {"launches": n, "ms": total}, ...} into buf
+ * (NUL-terminated, truncated to len); synchronises the recorded events. */
+int ddtm_timer_report(ddtm_ctx* ctx, char* buf, int len);
+
 #ifdef __cplusplus
 }
 #endif

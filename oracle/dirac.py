@@ -124,13 +124,18 @@ def site_term(U, kappa, c_sw):
 def apply_site(S, psi):
     """(S psi)(x) for a site-local 12x12 matrix field S and spinor psi (T,Z,Y,X,4,3)."""
     lat = psi.shape[:4]
-    return np.einsum('...ij,...j->...i', S, psi.reshape(lat + (12,))).reshape(psi.shape)
+    return np.matmul(S, psi.reshape(lat + (12, 1))).reshape(psi.shape)
 
 
 def apply_twist(psi, mu):
     """i mu Gamma5 psi with Gamma5 = I_V x gamma5 x I_C and gamma5 = diag(1,1,-1,-1)."""
     _, g5 = gamma_matrices()
-    return 1j * mu * np.einsum('st,...ta->...sa', g5, psi)
+    return 1j * mu * np.matmul(g5, psi)
+
+
+def colour_mul(U, psi):
+    """(U psi)(x): the colour matrix U(x) on every spin component, psi (...,4,3)."""
+    return np.matmul(psi, np.swapaxes(U, -1, -2))
 
 
 def apply_hopping(U, psi, bc_t=0, mask_from=None):
@@ -145,12 +150,10 @@ def apply_hopping(U, psi, bc_t=0, mask_from=None):
         Um = _link(U, mu)
         fwd = shift_fermion(psi, mu, +1, bc_t)
         # U_mu(x) acts on colour, (I - gamma_mu) on spin
-        t = np.einsum('...ab,...sb->...sa', Um, fwd)
-        out -= 0.5 * np.einsum('st,...ta->...sa', i4 - g[mu], t)
+        out -= 0.5 * np.matmul(i4 - g[mu], colour_mul(Um, fwd))
         bwd = shift_fermion(psi, mu, -1, bc_t)
         Ub = dagger(shift(Um, mu, -1))  # U_mu(x - mu)^dagger
-        t = np.einsum('...ab,...sb->...sa', Ub, bwd)
-        out -= 0.5 * np.einsum('st,...ta->...sa', i4 + g[mu], t)
+        out -= 0.5 * np.matmul(i4 + g[mu], colour_mul(Ub, bwd))
     return out
 
 

@@ -43,10 +43,13 @@ class FineOperator:
         return self.S + 1j * mu * np.diag(self._g5_12)
 
     def site_inv(self, psi, mu):
-        """Per-site inverse of the site-local part (solved by LU per site)."""
+        """Per-site inverse of the site-local part, applied as (S + i mu gamma5)^-1 psi.
+        The per-site inverses (library LU inversion) are kept for the last mu."""
+        if getattr(self, "_inv_mu", None) != mu:
+            self._inv = np.linalg.inv(self.site_matrix(mu))
+            self._inv_mu = mu
         lat = psi.shape[:4]
-        x = np.linalg.solve(self.site_matrix(mu), psi.reshape(lat + (12, 1)))
-        return x.reshape(psi.shape)
+        return np.matmul(self._inv, psi.reshape(lat + (12, 1))).reshape(psi.shape)
 
     def hop(self, psi):
         return dirac.apply_hopping(self.U, psi, self.bc_t)
@@ -58,12 +61,10 @@ class FineOperator:
         i4 = np.eye(4)
         if sign > 0:
             nb = dirac.shift_fermion(psi, d, +1, self.bc_t)
-            t = np.einsum('...ab,...sb->...sa', U, nb)
-            return -0.5 * np.einsum('st,...ta->...sa', i4 - self._g[d], t)
+            return -0.5 * np.matmul(i4 - self._g[d], dirac.colour_mul(U, nb))
         nb = dirac.shift_fermion(psi, d, -1, self.bc_t)
         Ub = dirac.dagger(dirac.shift(U, d, -1))
-        t = np.einsum('...ab,...sb->...sa', Ub, nb)
-        return -0.5 * np.einsum('st,...ta->...sa', i4 + self._g[d], t)
+        return -0.5 * np.matmul(i4 + self._g[d], dirac.colour_mul(Ub, nb))
 
     def gamma5(self, psi):
         return dirac.apply_Gamma5(psi)
@@ -91,7 +92,7 @@ class CoarseOperator:
         self.g5c = np.concatenate([np.ones(nv), -np.ones(nv)])  # Gamma5_c = tau3 x I_Nv
 
     def _mv(self, A, v):
-        return np.einsum('...ij,...j->...i', A, v)
+        return np.matmul(A, v[..., None])[..., 0]
 
     def site(self, v, mu):
         out = self._mv(self.blocks[0], v)
@@ -103,9 +104,10 @@ class CoarseOperator:
         return self.blocks[0] + 1j * mu * np.diag(self.g5c)
 
     def site_inv(self, v, mu):
-        lat = v.shape[:4]
-        x = np.linalg.solve(self.site_matrix(mu), v.reshape(lat + (2 * self.nv, 1)))
-        return x.reshape(v.shape)
+        if getattr(self, "_inv_mu", None) != mu:
+            self._inv = np.linalg.inv(self.site_matrix(mu))
+            self._inv_mu = mu
+        return self._mv(self._inv, v)
 
     def hop_dir(self, v, d, sign):
         idx = 1 + 2 * d if sign > 0 else 2 + 2 * d

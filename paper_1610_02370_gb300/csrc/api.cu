@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "solver.h"
+#include "timer.h"
 
 using namespace ddtm;
 
@@ -313,6 +314,26 @@ int ddtm_apply_D_field(ddtm_ctx* ctx, ddtm_field* y, const ddtm_field* x, double
   if (!x || !y || x->ctx != ctx || y->ctx != ctx || x->prec != y->prec || x->nrhs != y->nrhs || x == y)
     throw Error(DDTM_ERR_ARG, "fields must differ and share context, precision and nrhs");
   dslash_field(ctx, y, x, mu);
+  API_END(ctx)
+}
+
+int ddtm_timer_enable(ddtm_ctx* ctx, int on) {
+  API_BEGIN(ctx)
+  timer_enable(on != 0);
+  API_END(ctx)
+}
+
+int ddtm_timer_reset(ddtm_ctx* ctx) {
+  API_BEGIN(ctx)
+  timer_reset();
+  API_END(ctx)
+}
+
+int ddtm_timer_report(ddtm_ctx* ctx, char* buf, int len) {
+  API_BEGIN(ctx)
+  if (!buf || len <= 0) throw Error(DDTM_ERR_ARG, "invalid buffer");
+  std::string r = timer_report_json();
+  snprintf(buf, (size_t)len, "%s", r.c_str());
   API_END(ctx)
 }
 

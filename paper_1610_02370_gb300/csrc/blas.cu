@@ -6,6 +6,7 @@
 // per site by k_field_convert.
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 #include "blas.h"
 
 namespace ddtm {
@@ -143,6 +144,7 @@ static unsigned stream_grid(size_t n) {
 Blas::Blas(cudaStream_t s, ScratchPool* pool) : st(s), pool(pool) {}
 
 void Blas::dots(const void* V, int tv, size_t ldv, int nvec, const void* w, int tw, size_t n, double2* out_host) {
+  ScopedTimer timer_("blas_dots", st);
   int grid = RED_GRID;
   double2* partial = (double2*)pool->get("blas_partial", (size_t)nvec * grid * sizeof(double2));
   double2* dres = (double2*)pool->get("blas_result", (size_t)nvec * sizeof(double2));
@@ -171,6 +173,7 @@ double Blas::norm2(const void* a, int t, size_t n) {
 
 void Blas::multi_axpy(void* w, int tw, const void* V, int tv, size_t ldv, int nvec, const double2* h_host, size_t n,
                       double sign) {
+  ScopedTimer timer_("blas_multi_axpy", st);
   if (nvec <= 0) return;
   if (nvec > 256) throw Error(DDTM_ERR_ARG, "internal: multi_axpy limited to 256 vectors");
   double2* dh = (double2*)pool->get("blas_coef", 256 * sizeof(double2));
@@ -186,6 +189,7 @@ void Blas::multi_axpy(void* w, int tw, const void* V, int tv, size_t ldv, int nv
 }
 
 void Blas::axpby(double2 a, const void* x, int tx, double2 b, void* y, int ty, size_t n) {
+  ScopedTimer timer_("blas_axpby", st);
   unsigned grid = stream_grid(n);
   if (tx == 1 && ty == 1) k_axpby<float2, float2><<<grid, 256, 0, st>>>(a, (const float2*)x, b, (float2*)y, n);
   else if (tx == 0 && ty == 0) k_axpby<double2, double2><<<grid, 256, 0, st>>>(a, (const double2*)x, b, (double2*)y, n);
@@ -196,6 +200,7 @@ void Blas::axpby(double2 a, const void* x, int tx, double2 b, void* y, int ty, s
 
 void launch_field_convert(const FineGeom& g, int pin, const void* in, const float* inn, int pout, void* out, float* outn,
                           cudaStream_t st) {
+  ScopedTimer timer_("field_convert", st);
   unsigned grid = (unsigned)((g.V + 127) / 128);
 #define CONV(A, B, SA, SB)                                                                          \
   k_field_convert<A, B><<<grid, 128, 0, st>>>(Spinor<B>{(SB*)out, outn, g.Vb}, Spinor<A>{(SA*)in, (float*)inn, g.Vb}, g.V)

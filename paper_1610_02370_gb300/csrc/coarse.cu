@@ -11,6 +11,7 @@
 // the shifted coarsest twist delta*mu.
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 #include "coarse.h"
 
 namespace ddtm {
@@ -113,6 +114,7 @@ __global__ void k_galerkin(DS* __restrict__ Dc, const float2* __restrict__ P, Li
 
 void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* Dc, const float2* P, const void* links32,
                      const void* clover32, int nv, cudaStream_t st) {
+  ScopedTimer timer_("galerkin", st);
   Geo q{g.Vb, g.Nb, g.loc_nbr.as<uint32_t>(), g.blk_nbr.as<int>()};
   FaceTables f;
   f.idx = faces.idx.as<int>();
@@ -310,12 +312,14 @@ static void coarse_apply_t(const CoarseLevel& c, cplx<float>* y, const cplx<floa
 
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, double mu_c, int mode, float sres,
                               float sy, cudaStream_t st) {
+  ScopedTimer timer_("coarse_apply", st);
   if (c.prec == PREC_F16) coarse_apply_t<__half2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, mu_c, mode, sres, sy, st);
   else coarse_apply_t<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, mu_c, mode, sres, sy, st);
 }
 
 void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e,
                              double mu_c, int mode, float sres, float sy, cudaStream_t st) {
+  ScopedTimer timer_("coarse_apply_odd", st);
   int no = (int)c.h_odd.size();
   if (c.prec == PREC_F16)
     coarse_apply_t<__half2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, mu_c, mode, sres, sy, st);
@@ -325,6 +329,7 @@ void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<
 
 void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, float sr,
                         float sh, cudaStream_t st) {
+  ScopedTimer timer_("coarse_even", st);
   int spb = spb_for(c.n);
   int ne = (int)c.h_even.size();
   unsigned grid = (unsigned)((ne + spb - 1) / spb);
@@ -339,6 +344,7 @@ void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>*
 }
 
 void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int dir, cudaStream_t st) {
+  ScopedTimer timer_("parity_copy", st);
   int cnt = parity == 0 ? (int)c.h_even.size() : (int)c.h_odd.size();
   const int* list = parity == 0 ? c.even.as<int>() : c.odd.as<int>();
   size_t tot = (size_t)cnt * c.n;
@@ -347,6 +353,7 @@ void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, 
 }
 
 void launch_self_inverse(CoarseLevel& c, double mu_c, cudaStream_t st) {
+  ScopedTimer timer_("self_inverse", st);
   int ne = (int)c.h_even.size();
   c.Dinv.ensure((size_t)ne * c.n * c.n * sizeof(float2));
   size_t smem = (size_t)c.n * 2 * c.n * sizeof(cplx<double>);

@@ -14,6 +14,7 @@
 //   twist; storage FP64 / FP32 / FP16 (per-site scaled spinors).
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 
 namespace ddtm {
 
@@ -193,6 +194,7 @@ __global__ void k_clover_build(double2* __restrict__ out, const double2* __restr
 
 void launch_clover_build(const FineGeom& g, double* clov, const double* Ucanon, double m_plus_4, double csw,
                          cudaStream_t s) {
+  ScopedTimer timer_("clover_build", s);
   upload_gg();
   Lat l;
   BlockMap m;
@@ -264,6 +266,7 @@ __global__ void k_site_inverse(typename Prec<P>::store2* __restrict__ out, const
 }
 
 void launch_site_inverse(const FineGeom& g, int prec, void* out, const double* clov64, double mu, cudaStream_t s) {
+  ScopedTimer timer_("site_inverse", s);
   long n = (long)g.Nb * g.Vb;  // Nb * Vh * 2
   unsigned grid = (unsigned)((n + 127) / 128);
   if (prec == PREC_F64) k_site_inverse<PREC_F64><<<grid, 128, 0, s>>>((double2*)out, (const double2*)clov64, g.Vb, g.Nb, mu);
@@ -332,6 +335,7 @@ static Geo make_geo(const FineGeom& g) {
 
 void launch_dslash(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
                    const void* links, const void* clover, double mu, cudaStream_t s) {
+  ScopedTimer timer_("dslash", s);
   Geo q = make_geo(g);
   unsigned grid = (unsigned)((g.V + 127) / 128);
   if (prec == PREC_F64) {

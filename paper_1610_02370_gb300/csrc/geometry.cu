@@ -9,6 +9,7 @@
 // alternating parities, which makes (parity, lexloc >> 1) a bijection.
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 
 namespace ddtm {
 
@@ -257,6 +258,7 @@ __global__ void k_links_from_canon(double2* __restrict__ out, const double2* __r
 static unsigned grid_for(long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 void launch_spinor_from_canon(const FineGeom& g, int prec, void* d, float* nrm, const double* in, cudaStream_t s) {
+  ScopedTimer timer_("layout_in", s);
   CanonMap m = make_map(g);
   unsigned grid = grid_for(g.V, 128);
   const double2* src = reinterpret_cast<const double2*>(in);
@@ -274,6 +276,7 @@ void launch_spinor_from_canon(const FineGeom& g, int prec, void* d, float* nrm, 
 }
 
 void launch_spinor_to_canon(const FineGeom& g, int prec, const void* d, const float* nrm, double* out, cudaStream_t s) {
+  ScopedTimer timer_("layout_out", s);
   CanonMap m = make_map(g);
   unsigned grid = grid_for(g.V, 128);
   double2* dst = reinterpret_cast<double2*>(out);

@@ -16,6 +16,7 @@
 // products are reduced per CTA in a fixed order (deterministic).
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 #include "stencil.cuh"
 
 namespace ddtm {
@@ -215,6 +216,7 @@ static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void*
 void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,
                      const void* clover, const void* sinv, const int* blocks, const int* zero_blocks, int nblocks,
                      int zero_x, int nmr, double mu, cudaStream_t s) {
+  ScopedTimer timer_("sap_half", s);
   if (prec == PREC_F64)
     launch_sap_half_t<PREC_F64>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, s);
   else if (prec == PREC_F32)

@@ -1,0 +1,92 @@
+#include <map>
+#include <vector>
+
+#include "ddtm_internal.h"
+#include "timer.h"
+
+namespace ddtm {
+
+namespace {
+struct Rec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct State {
+  bool on = false;
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<long, double>> acc;
+  const char* cur = nullptr;
+  cudaEvent_t cur_a = nullptr;
+};
+State& S() {
+  static State s;
+  return s;
+}
+cudaEvent_t get_event() {
+  State& s = S();
+  if (!s.pool.empty()) {
+    cudaEvent_t e = s.pool.back();
+    s.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+void flush() {
+  State& s = S();
+  for (auto& r : s.pending) {
+    CK(cudaEventSynchronize(r.b));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    auto& v = s.acc[r.name];
+    v.first += 1;
+    v.second += ms;
+    s.pool.push_back(r.a);
+    s.pool.push_back(r.b);
+  }
+  s.pending.clear();
+}
+}  // namespace
+
+bool timer_on() { return S().on; }
+void timer_enable(bool on) {
+  if (!on) flush();
+  S().on = on;
+}
+void timer_reset() {
+  flush();
+  S().acc.clear();
+}
+std::string timer_report_json() {
+  flush();
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : S().acc) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %ld, \"ms\": %.6f}", first ? "" : ", ", kv.first.c_str(),
+             kv.second.first, kv.second.second);
+    out += buf;
+    first = false;
+  }
+  return out + "}";
+}
+
+ScopedTimer::ScopedTimer(const char* name, cudaStream_t s) : active(S().on), st(s) {
+  if (!active) return;
+  State& g = S();
+  if (g.pending.size() > 20000) flush();
+  g.cur = name;
+  g.cur_a = get_event();
+  CK(cudaEventRecord(g.cur_a, s));
+}
+
+ScopedTimer::~ScopedTimer() {
+  if (!active) return;
+  State& g = S();
+  cudaEvent_t b = get_event();
+  if (cudaEventRecord(b, st) == cudaSuccess) g.pending.push_back(Rec{g.cur, g.cur_a, b});
+}
+
+}  // namespace ddtm

@@ -7,6 +7,7 @@
 // Coarse vectors: complex FP32 [site][2 nv], dof s*nv + i.
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 
 namespace ddtm {
 
@@ -80,6 +81,7 @@ __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv,
 }
 
 void launch_build_P(const FineGeom& g, float2* P, const float2* tv, int nv, cudaStream_t st) {
+  ScopedTimer timer_("build_P", st);
   int threads = ((g.Vb + 31) / 32) * 32;
   k_build_P<<<g.Nb * 2, threads, 0, st>>>(P, tv, nv, g.Vb, g.V);
   CKL("build_P");
@@ -186,12 +188,14 @@ static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cpl
 
 void launch_restrict(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const void* P,
                      int pprec, int nv, cudaStream_t st) {
+  ScopedTimer timer_("restrict", st);
   if (pprec == PREC_F16) restrict_t<__half2>(g, pin, c, psi, pn, (const __half2*)P, nv, st);
   else restrict_t<float2>(g, pin, c, psi, pn, (const float2*)P, nv, st);
 }
 
 void launch_prolong(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const void* P, int pprec,
                     int nv, int add, cudaStream_t st) {
+  ScopedTimer timer_("prolong", st);
   if (pprec == PREC_F16) prolong_t<__half2>(g, pout, x, xn, e, (const __half2*)P, nv, add, st);
   else prolong_t<float2>(g, pout, x, xn, e, (const float2*)P, nv, add, st);
 }

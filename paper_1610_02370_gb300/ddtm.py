@@ -75,6 +75,9 @@ SIGNATURES = {
     "ddtm_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(ddtm_solve_info)]),
     "ddtm_save_setup": (_I, [_P, ctypes.c_char_p]),
     "ddtm_load_setup": (_I, [_P, ctypes.c_char_p]),
+    "ddtm_timer_enable": (_I, [_P, _I]),
+    "ddtm_timer_reset": (_I, [_P]),
+    "ddtm_timer_report": (_I, [_P, ctypes.c_char_p, _I]),
 }
 for _name, (_res, _args) in SIGNATURES.items():
     _f = getattr(_lib, _name)
@@ -258,3 +261,19 @@ def ddtm_save_setup(ctx, path):
 
 def ddtm_load_setup(ctx, path):
     _check(ctx, _lib.ddtm_load_setup(ctx, path.encode()))
+
+
+def ddtm_timer_enable(ctx, on):
+    _check(ctx, _lib.ddtm_timer_enable(ctx, 1 if on else 0))
+
+
+def ddtm_timer_reset(ctx):
+    _check(ctx, _lib.ddtm_timer_reset(ctx))
+
+
+def ddtm_timer_report(ctx):
+    """Per-kernel {name: {"launches": n, "ms": total}} since the last reset."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(ctx, _lib.ddtm_timer_report(ctx, buf, len(buf)))
+    return json.loads(buf.value.decode())
