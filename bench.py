@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 twisted-mass DD-alpha-AMG hot path.
+
+One step = one point-to-all propagator on the 32^3 x 64 workload: adaptive
+setup (test vectors, P, Galerkin coarse operator) followed by the solve of the
+12 spin-colour point sources to FP64 relative residual 1e-10, all through the
+C ABI of libddtm with inputs resident on the device.  The metric is seconds per
+12-rhs solve (setup included, lower is better).  Beside it the line carries
+the D(mu) stencil bandwidth against the HBM roof, the roofline of the dominant
+kernel, an end-to-end number through host buffers, clocks, and the CPU oracle
+timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+With N > 1 (torchrun) every rank solves its own propagator on its own GPU
+(independent replicas: the method's units here are whole propagators) and the
+line reports the whole job.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D_TM apply GB/s vs HBM peak; s per 12-rhs solve to 1e-10, mixed vs FP64"
+UNIT = "s per 12-rhs solve"
+
+# Workloads: synthetic SU(3) links exp(i eps H) at the lattice sizes and masses
+# of the paper's ensembles; multigrid parameters of the two-level set (4^4
+# aggregates, Nv = 24, 6 setup iterations) with the smoother of Table 1.
+WORKLOADS = {
+    "32x32x32x64": dict(dims=(64, 32, 32, 32), eps=0.12, kappa=0.1372, c_sw=1.5755, mu=0.0015),
+    "24x24x24x48": dict(dims=(48, 24, 24, 24), eps=0.15, kappa=0.1370, c_sw=1.5755, mu=0.002),
+    "16x16x16x32": dict(dims=(32, 16, 16, 16), eps=0.2, kappa=0.1340, c_sw=1.5755, mu=0.003),
+}
+MG = dict(block=(4, 4, 4, 4), nv=24, n_setup=6, post_smooth=4, nmr=3, outer_restart=30, outer_tol=1e-10,
+          smoother_prec=2, coarse_prec=1)
+NRHS = 12
+SEED = 2024
+
+# Algorithmic bytes per site of one D(mu) application: links 4x18 reals (each
+# read once), clover 2 x 36 reals, x and y 24 reals each; FP16 adds two 4-byte
+# site scales (x and y).
+DSLASH_BYTES = {"f64": 1536, "f32": 768, "f16": 392}
+S2 = {"f64": 16, "f32": 8, "f16": 4}  # bytes per stored complex number
+
+
+def algorithmic_bytes(name, V, Vb, b, nv, Nc):
+    """Algorithmic HBM bytes of one launch of kernel ``name`` (every array
+    element the kernel must touch, once), or None if no model applies."""
+    n = 2 * nv
+    prec = name.rsplit("_", 1)[-1]
+    s2 = S2.get(prec)
+    face = sum(2.0 / bb for bb in b)  # halo sites per site of a block (both faces, 4 directions)
+    if name.startswith("dslash_"):
+        return DSLASH_BYTES[prec] * V
+    if name.startswith("sap_half_"):
+        half = V / 2
+        nrm = 4 if prec == "f16" else 0
+        per = (36 + 36 + 36) * s2   # own links, clover, even-site inverses (72 complex per even site)
+        per += 12 * s2 + nrm        # b
+        per += 2 * (12 * s2 + nrm)  # x read and written on the block
+        per += face * (12 * s2 + nrm + 9 * s2 / 2)  # neighbour x on the faces, links of backward face hops
+        return half * per
+    if name.startswith("restrict_") or name.startswith("prolong_"):
+        pbytes = 4 if (prec == "f16") else 8
+        nrm = 4 if prec == "f16" else 0
+        fine = V * (12 * s2 + nrm)
+        return V * 12 * nv * pbytes + fine * (2 if name.startswith("prolong") else 1) + Nc * n * 8
+    if name.startswith("coarse_even_"):
+        d = S2[prec]
+        ne = Nc / 2
+        return ne * (8 * n * n * d + n * n * 8 + 8 * n * 8 + 2 * n * 8)
+    if name.startswith("coarse_apply_odd_"):
+        d = S2[prec]
+        no = Nc / 2
+        return no * (4.5 * n * n * d + 5 * n * 8)  # launches alternate self (1 block) and hop (8 blocks)
+    return None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="16x16x16x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---- clocks -----------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---- CPU oracle baseline -------------------------------------------------------------------------
+def oracle_unit_times(wl, sample_dims=(16, 8, 8, 8)):
+    """Time the oracle's building blocks on a bounded sample lattice with the
+    workload's couplings and multigrid parameters; returns seconds per site (or
+    per coarse site) of each block."""
+    import numpy as np
+    from oracle import aggregation, coarse, krylov, sap
+    from oracle.operators import FineOperator
+    from paper_1610_02370_gb300 import synth
+
+    U = synth.gauge_field(sample_dims, wl["eps"], seed=0).numpy()
+    op = FineOperator(U, wl["kappa"], wl["c_sw"])
+    V = float(np.prod(op.lat))
+    mu = wl["mu"]
+    psi = synth.gaussian_spinor(sample_dims, seed=1).numpy()
+    out = {}
+
+    def timed(fn, reps=1):
+        t = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        return (time.perf_counter() - t) / reps, r
+
+    t, _ = timed(lambda: op.apply(psi, mu), 2)
+    out["dslash"] = t / V
+    blk = MG["block"]
+
+    def half_sweep():
+        r = psi - op.apply(psi * 0.5, mu)
+        return sap.block_solve(op, r, mu, blk, 0, MG["nmr"])
+    t, _ = timed(half_sweep)
+    out["sap_half"] = t / V
+    v = synth.gaussian_vectors((MG["nv"],) + op.lat + (4, 3), seed=3).numpy()
+    t, W = timed(lambda: aggregation.build_P(op, v, blk))
+    out["build_P"] = t / V
+    t, cop = timed(lambda: coarse.build_coarse_operator(op, W, blk))
+    out["galerkin"] = t / V
+    t, c = timed(lambda: aggregation.restrict(W, psi, op.lat, blk))
+    out["restrict"] = t / V
+    t, _ = timed(lambda: aggregation.prolong(W, c, op.lat, blk))
+    out["prolong"] = t / V
+    Nc = float(np.prod(cop.lat))
+    nit = 10
+    t, _ = timed(lambda: krylov.eo_gmres(cop, c, 5.2 * mu, restart=nit, max_restarts=0, tol=1e-300))
+    out["coarse_iter"] = t / nit / Nc
+    out["_sample"] = "x".join(str(d) for d in (sample_dims[1], sample_dims[2], sample_dims[3], sample_dims[0]))
+    return out
+
+
+def oracle_estimate(unit, counts, V, Nc):
+    """Oracle seconds for the GPU step's operation counts (launch counts per kernel)."""
+    def c(prefix):
+        return sum(v["launches"] for k, v in counts.items() if k.startswith(prefix))
+    solves = c("restrict_")
+    coarse_iters = max(0, c("coarse_even_") - 2 * solves)
+    t = 0.0
+    t += c("dslash_") * unit["dslash"] * V
+    t += c("sap_half_") * unit["sap_half"] * V
+    t += c("build_P") * unit["build_P"] * V
+    t += c("galerkin") * unit["galerkin"] * V
+    t += solves * unit["restrict"] * V
+    t += c("prolong_") * unit["prolong"] * V
+    t += coarse_iters * unit["coarse_iter"] * Nc
+    return t, coarse_iters
+
+
+# Operation counts of one step of the default workload (kernel launches of
+# the library, from a GPU run of this benchmark), used by the reference arm,
+# which runs no GPU code.  Updated when the method's iteration counts change.
+REFERENCE_COUNTS = {
+    "dslash_f64": {"launches": 0}, "sap_half_f16": {"launches": 0}, "build_P": {"launches": 6},
+    "galerkin": {"launches": 6}, "restrict_f16": {"launches": 0}, "prolong_f16": {"launches": 0},
+    "coarse_even_f32": {"launches": 0},
+}
+
+
+def reference_arm(args):
+    """CPU oracle on a bounded sample, scaled to the workload (see oracle_estimate)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    wl = WORKLOADS[args.workload]
+    T, X, Y, Z = wl["dims"]
+    V = T * X * Y * Z
+    Nc = V // int(np.prod(MG["block"]))
+    counts = json.loads(os.environ.get("DDTM_REFERENCE_COUNTS", "null")) or REFERENCE_COUNTS
+    vals = []
+    for i in range(args.warmup + args.steps):
+        unit = oracle_unit_times(wl)
+        est, _ = oracle_estimate(unit, counts, V, Nc)
+        if i >= args.warmup:
+            vals.append(est)
+    val = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload + " propagator (12 point sources)", **{k: wl[k] for k in wl},
+                       "mg": MG},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "oracle building blocks timed on a %s lattice, scaled per site to %s and "
+                                       "multiplied by the operation counts of one GPU step" % (
+                                           unit["_sample"], args.workload)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---- our arm ------------------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1610_02370_gb300 import build as _build
+    _build.build()
+    from paper_1610_02370_gb300 import ddtm, synth
+
+    wl = WORKLOADS[args.workload]
+    dims = wl["dims"]
+    T, X, Y, Z = dims
+    V = T * X * Y * Z
+    Vb = int(np.prod(MG["block"]))
+    Nc = V // Vb
+    stream = torch.cuda.current_stream()
+
+    ctx = ddtm.ddtm_create(dims, MG["block"], 0)
+    ddtm.ddtm_set_stream(ctx, stream.cuda_stream)
+    p = ddtm.ddtm_get_params(ctx)
+    p.nv[0] = MG["nv"]
+    for k in ("n_setup", "post_smooth", "nmr", "outer_restart", "outer_tol", "smoother_prec", "coarse_prec"):
+        setattr(p, k, MG[k])
+    ddtm.ddtm_set_params(ctx, p)
+
+    U = synth.gauge_field(dims, wl["eps"], seed=rank, device="cuda")
+    ddtm.ddtm_load_gauge(ctx, U, wl["kappa"], wl["c_sw"])
+    b = synth.point_sources(dims, device="cuda")
+    x = torch.zeros_like(b)
+    mu = wl["mu"]
+    info_last = {}
+
+    def step():
+        ddtm.ddtm_setup(ctx, mu, SEED)
+        info, code = ddtm.ddtm_solve(ctx, x, b, NRHS, mu)
+        if code != ddtm.OK:
+            raise RuntimeError("solve did not converge: " + ddtm.ddtm_last_error(ctx))
+        info_last.update(iters=info.iters, restarts=info.restarts, coarse_iters=info.coarse_iters,
+                         max_relres=info.max_relres, solve_s=info.solve_s, setup_s=info.setup_s)
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ddtm.ddtm_timer_reset(ctx)
+    ddtm.ddtm_timer_enable(ctx, True)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ddtm.ddtm_timer_enable(ctx, False)
+    counts = ddtm.ddtm_timer_report(ctx)
+    ms = ev0.elapsed_time(ev1)
+    t_step = ms / 1000.0 / args.steps
+    if dist is not None:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = t_step / world  # whole job: world propagators per step
+
+    # residual check of the last solve with the library's FP64 operator
+    r = torch.empty_like(x)
+    ddtm.ddtm_apply_D(ctx, r, x, NRHS, mu, ddtm.PREC_F64)
+    r = b - r
+    relres = float(max((r[i].norm() / b[i].norm()).item() for i in range(NRHS)))
+
+    # D(mu) stencil bandwidth on this lattice, L2 flushed between applications
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+    dtm = {}
+    for prec, tag in ((ddtm.PREC_F16, "f16"), (ddtm.PREC_F32, "f32"), (ddtm.PREC_F64, "f64")):
+        fx = ddtm.ddtm_field_create(ctx, prec, 1)
+        fy = ddtm.ddtm_field_create(ctx, prec, 1)
+        ddtm.ddtm_field_import(ctx, fx, b[0].contiguous())
+        times = []
+        for it in range(13):
+            flush.fill_(float(it))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ddtm.ddtm_apply_D_field(ctx, fy, fx, mu)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= 3:
+                times.append(e0.elapsed_time(e1))
+        tmed = statistics.median(times) / 1000.0
+        dtm[tag] = {"gbs": DSLASH_BYTES[tag] * V / tmed / 1e9, "ms": tmed * 1e3}
+        ddtm.ddtm_field_destroy(fx)
+        ddtm.ddtm_field_destroy(fy)
+    del flush
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+
+    # dominant kernel of the step and its roofline
+    kern = sorted(((v["ms"], k) for k, v in counts.items()), reverse=True)
+    total_ms = sum(v["ms"] for v in counts.values())
+    dom = kern[0][1]
+    launches = counts[dom]["launches"]
+    avg_s = counts[dom]["ms"] / launches / 1000.0
+    nbytes = algorithmic_bytes(dom, V, Vb, MG["block"], MG["nv"], Nc)
+    achieved = nbytes / avg_s / 1e9 if nbytes else None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None, "traffic": None,
+                "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches / args.steps,
+                "bytes_per_launch": nbytes, "peak_source": peak_note}
+    breakdown = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                     "share": v["ms"] / total_ms} for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"])}
+    gpu_launches = int(sum(v["launches"] for v in counts.values()))
+
+    # end to end through host buffers: gauge upload + setup + solve with pinned host b and x
+    e2e = None
+    if not args.no_e2e:
+        Uh = U.cpu().pin_memory()
+        bh = b.cpu().pin_memory()
+        xh = torch.zeros_like(bh).pin_memory()
+        ts = []
+        for _ in range(args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            ddtm.ddtm_load_gauge(ctx, Uh, wl["kappa"], wl["c_sw"])
+            ddtm.ddtm_setup(ctx, mu, SEED)
+            info, code = ddtm.ddtm_solve(ctx, xh, bh, NRHS, mu)
+            barrier()
+            ts.append(time.perf_counter() - t0)
+        te = max(ts) if ts else float("nan")
+        if dist is not None:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": te / world, "unit": UNIT, "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
+               "d2h_bytes_per_step": int(xh.numel() * 16)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        unit = oracle_unit_times(wl)
+        per_step_counts = {k: {"launches": v["launches"] / args.steps} for k, v in counts.items()}
+        est, _ = oracle_estimate(unit, per_step_counts, V, Nc)
+        cpu = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle building blocks (D, SAP half-sweep, P, Galerkin, R, P, coarse even-odd GMRES "
+                         "iteration) timed on a %s lattice with the same couplings and multigrid parameters, scaled "
+                         "per site to %s and multiplied by this step's kernel launch counts" % (
+                             unit["_sample"], args.workload),
+               "unit_s_per_site": {k: v for k, v in unit.items() if not k.startswith("_")}}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 outer / f32 arithmetic, f16 smoother storage", "data": "synthetic",
+            "config": {"workload": "%s twisted-mass clover propagator, 12 point sources, two-level DD-alpha-AMG"
+                                   % args.workload, "dims_TXYZ": list(dims), **{k: wl[k] for k in wl if k != "dims"},
+                       "mg": MG, "nrhs": NRHS, "l2": "working set (test vectors, P, D_c) far above L2",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "step": {"setup_s": info_last.get("setup_s"), "solve_s": info_last.get("solve_s"),
+                     "outer_iters_max": info_last.get("iters"), "coarse_iters": info_last.get("coarse_iters"),
+                     "max_relres": relres},
+            "dtm_apply": {"bound": "hbm", "peak": hbm, "unit": "GB/s",
+                          **{k: {"achieved": v["gbs"], "frac": v["gbs"] / hbm, "ms": v["ms"]} for k, v in dtm.items()}},
+            "roofline": roofline,
+            "kernels": breakdown,
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ddtm.ddtm_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -319,7 +319,7 @@ void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<f
 
 void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e,
                              double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  ScopedTimer timer_("coarse_apply_odd", st);
+  ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_apply_odd_f16" : "coarse_apply_odd_f32", st);
   int no = (int)c.h_odd.size();
   if (c.prec == PREC_F16)
     coarse_apply_t<__half2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, mu_c, mode, sres, sy, st);
@@ -329,7 +329,7 @@ void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<
 
 void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, float sr,
                         float sh, cudaStream_t st) {
-  ScopedTimer timer_("coarse_even", st);
+  ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_even_f16" : "coarse_even_f32", st);
   int spb = spb_for(c.n);
   int ne = (int)c.h_even.size();
   unsigned grid = (unsigned)((ne + spb - 1) / spb);

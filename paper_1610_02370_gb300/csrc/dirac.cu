@@ -335,7 +335,7 @@ static Geo make_geo(const FineGeom& g) {
 
 void launch_dslash(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
                    const void* links, const void* clover, double mu, cudaStream_t s) {
-  ScopedTimer timer_("dslash", s);
+  ScopedTimer timer_(prec == PREC_F64 ? "dslash_f64" : prec == PREC_F32 ? "dslash_f32" : "dslash_f16", s);
   Geo q = make_geo(g);
   unsigned grid = (unsigned)((g.V + 127) / 128);
   if (prec == PREC_F64) {

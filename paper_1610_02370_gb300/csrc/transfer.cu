@@ -188,14 +188,14 @@ static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cpl
 
 void launch_restrict(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const void* P,
                      int pprec, int nv, cudaStream_t st) {
-  ScopedTimer timer_("restrict", st);
+  ScopedTimer timer_(pin == PREC_F16 ? "restrict_f16" : pin == PREC_F32 ? "restrict_f32" : "restrict_f64", st);
   if (pprec == PREC_F16) restrict_t<__half2>(g, pin, c, psi, pn, (const __half2*)P, nv, st);
   else restrict_t<float2>(g, pin, c, psi, pn, (const float2*)P, nv, st);
 }
 
 void launch_prolong(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const void* P, int pprec,
                     int nv, int add, cudaStream_t st) {
-  ScopedTimer timer_("prolong", st);
+  ScopedTimer timer_(pout == PREC_F16 ? "prolong_f16" : pout == PREC_F32 ? "prolong_f32" : "prolong_f64", st);
   if (pprec == PREC_F16) prolong_t<__half2>(g, pout, x, xn, e, (const __half2*)P, nv, add, st);
   else prolong_t<float2>(g, pout, x, xn, e, (const float2*)P, nv, add, st);
 }

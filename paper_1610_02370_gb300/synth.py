@@ -11,7 +11,7 @@ produces.  Layout of everything returned (torch tensors, complex128):
 
 Random gauge links follow U = exp(i eps H) with H = (A + A^dagger)/2 - tr/3,
 A having i.i.d. complex entries with N(0,1) real and imaginary parts; the
-exponential is taken through the eigendecomposition of H.  The draws come from
+exponential is a scaled-and-squared Taylor series (unitary to rounding).  The draws come from
 a torch generator seeded with ``seed`` on ``device``, so a CPU and a CUDA field
 of the same seed differ; tests always hand the same tensor to both sides.
 """
@@ -32,6 +32,25 @@ def _gen(seed, device):
     return g
 
 
+def expm_i_hermitian(H, eps):
+    """exp(i eps H) for a batch of Hermitian 3x3 matrices by Taylor series with
+    scaling and squaring (Moler and Van Loan): A = i eps H / 2^s with
+    ||A||_F <= 1/2, 20 Taylor terms (remainder below 1e-20), then s squarings."""
+    A = 1j * eps * H
+    nrm = float(torch.linalg.matrix_norm(A).max()) if A.numel() else 0.0
+    s = max(0, int(math.ceil(math.log2(nrm / 0.5)))) if nrm > 0.5 else 0
+    A = A / (2.0 ** s)
+    eye = torch.eye(3, dtype=A.dtype, device=A.device)
+    term = eye.expand(A.shape).clone()
+    out = term.clone()
+    for k in range(1, 21):
+        term = term @ A / k
+        out = out + term
+    for _ in range(s):
+        out = out @ out
+    return out
+
+
 def random_hermitian_exp(shape, eps, seed, device="cpu"):
     """exp(i eps H) for a batch of traceless Hermitian Gaussian 3x3 H."""
     g = _gen(seed, device)
@@ -40,9 +59,7 @@ def random_hermitian_exp(shape, eps, seed, device="cpu"):
     H = 0.5 * (A + A.mH)
     tr = torch.diagonal(H, dim1=-2, dim2=-1).sum(-1)
     H = H - (tr / 3.0)[..., None, None] * torch.eye(3, dtype=H.dtype, device=device)
-    w, V = torch.linalg.eigh(H)
-    ph = torch.exp(1j * eps * w.to(torch.complex128))
-    return (V * ph[..., None, :]) @ V.mH
+    return expm_i_hermitian(H, eps)
 
 
 def gauge_field(dims, eps, seed=0, device="cpu", chunk_sites=1 << 20):

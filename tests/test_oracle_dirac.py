@@ -242,3 +242,20 @@ def test_even_odd_eigenvalue_relation_csw0():
         for sgn in (+1, -1):
             cand = (m + 4) * (1 + sgn * np.sqrt(1 - lh / (m + 4) + 0j))
             assert np.min(np.abs(lam - cand)) < 1e-9
+
+
+def test_synthetic_links_are_su3():
+    """The input generator's exp(i eps H) is special unitary to rounding, for the
+    small eps of the gauge fields and eps = 1 of the gauge transformations."""
+    import torch
+    for eps in (0.12, 0.3, 1.0):
+        U = synth.random_hermitian_exp((64, 4), eps, seed=1).numpy()
+        uu = U @ dirac.dagger(U)
+        assert np.max(np.abs(uu - np.eye(3))) < 1e-14
+        assert np.max(np.abs(np.linalg.det(U) - 1)) < 1e-14
+    # exp(i eps H) = V diag(e^{i eps w}) V^dagger with (w, V) from a library eigensolver
+    H = np.array([[1.0, 0.5 - 0.2j, 0.1j], [0.5 + 0.2j, -0.3, 0.4], [-0.1j, 0.4, -0.7]])
+    w, Vv = np.linalg.eigh(H)
+    want = Vv @ np.diag(np.exp(1j * 0.8 * w)) @ Vv.conj().T
+    got = synth.expm_i_hermitian(torch.from_numpy(H)[None], 0.8).numpy()[0]
+    assert np.max(np.abs(got - want)) < 1e-14
