@@ -144,6 +144,25 @@ int ddtm_apply_D(ddtm_ctx* ctx, double* y, const double* x, int nrhs, double mu,
 int ddtm_sap(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int ncycles, int nmr,
              int prec, int loc);
 
+/* y = D(mu) x like ddtm_apply_D, for one right-hand side held in device
+ * memory (canonical layout), without allocating anything during the call.
+ * Meant for callers that cannot call cudaMalloc: cudaMalloc and cudaFree may
+ * synchronise the whole device and stall their other streams, or the caller's
+ * own allocator already owns the device memory budget.  The paper has no
+ * counterpart; it is an interface convenience around the Sec. 2.1 operator.
+ * Working memory: one fixed 64 MiB device array inside the library (held by
+ * every GPU that loads the library until the process exits), enough for two
+ * internal-layout fields of up to 174762 sites in FP64 (e.g. 16^3 x 32);
+ * larger lattices return DDTM_ERR_ARG with the sizes in the message.  The
+ * first call on a device looks up the array's device address; make that call
+ * before any stream capture.  All calls share the array, which keeps the last
+ * call's contents (every byte a call reads it writes first), so calls that
+ * overlap on the GPU race.  Work is issued on the context's stream and not
+ * synchronised.  x and y must be distinct device pointers; the gauge field
+ * must already be held in precision prec (FP64 always is; one ddtm_apply_D
+ * call with F32 or F16 creates that copy), else DDTM_ERR_STATE. */
+int ddtm_apply_D_noalloc(ddtm_ctx* ctx, double* y, const double* x, double mu, int prec);
+
 /* ---- device-resident fine fields (internal layout) ------------------------ */
 
 /* A fine spinor field of nrhs right-hand sides held on the device in the

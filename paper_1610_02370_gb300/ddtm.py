@@ -57,6 +57,7 @@ SIGNATURES = {
     "ddtm_set_params": (_I, [_P, ctypes.POINTER(ddtm_params)]),
     "ddtm_load_gauge": (_I, [_P, _P, _I, _D, _D]),
     "ddtm_apply_D": (_I, [_P, _P, _P, _I, _D, _I, _I]),
+    "ddtm_apply_D_noalloc": (_I, [_P, _P, _P, _D, _I]),
     "ddtm_sap": (_I, [_P, _P, _P, _I, _D, _I, _I, _I, _I]),
     "ddtm_field_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
     "ddtm_field_destroy": (_I, [_P]),
@@ -169,6 +170,15 @@ def ddtm_load_gauge(ctx, U, kappa, c_sw):
 def ddtm_apply_D(ctx, y, x, nrhs, mu, prec):
     by, bx = _buf(y, True), _buf(x)
     _check(ctx, _lib.ddtm_apply_D(ctx, by[0], bx[0], nrhs, mu, prec, _same_loc(by, bx)))
+
+
+def ddtm_apply_D_noalloc(ctx, y, x, mu, prec):
+    """y = D(mu) x for one right-hand side in device memory, with no allocation
+    during the call (fixed scratch inside the library; see include/ddtm.h)."""
+    by, bx = _buf(y, True), _buf(x)
+    if _same_loc(by, bx) != LOC_DEVICE:
+        raise TypeError("ddtm_apply_D_noalloc takes device arrays")
+    _check(ctx, _lib.ddtm_apply_D_noalloc(ctx, by[0], bx[0], mu, prec))
 
 
 def ddtm_sap(ctx, x, b, nrhs, mu, ncycles, nmr, prec):
