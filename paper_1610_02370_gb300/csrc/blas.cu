@@ -1,18 +1,16 @@
-// Vector kernels for the Krylov solvers (Sec. 2.5): inner products with FP64
-// accumulation and a deterministic two-stage reduction (fixed grid, fixed
-// summation order), Gram-Schmidt multi-dots and multi-axpys, and element-wise
-// updates.  Vectors are plain complex arrays (float2 or double2); fine fields
-// of the internal layout qualify as they are.  FP16 fine fields are converted
-// per site by k_field_convert.
+// Vector kernels for the Krylov solvers (Sec. 2.5), batched over right-hand
+// sides: inner products with FP64 accumulation and a deterministic two-stage
+// reduction, Gram-Schmidt multi-dots and multi-axpys (fused with the norms of
+// the result), per-rhs scalings, and precision conversion of fine fields.
+// Layouts and type tags are described in blas.h.
+#include <string.h>
+
+#include "blas.h"
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "timer.h"
-#include "blas.h"
 
 namespace ddtm {
-
-static const int RED_GRID = 1024;  // CTAs of every reduction's first stage
-static const int RED_T = 256;
 
 template <typename T> __device__ __forceinline__ double2 ld2(const T* p, size_t i);
 template <> __device__ __forceinline__ double2 ld2<float2>(const float2* p, size_t i) { float2 a = p[i]; return make_double2(a.x, a.y); }
@@ -21,103 +19,145 @@ template <typename T> __device__ __forceinline__ void st2(T* p, size_t i, double
 template <> __device__ __forceinline__ void st2<float2>(float2* p, size_t i, double re, double im) { p[i] = make_float2((float)re, (float)im); }
 template <> __device__ __forceinline__ void st2<double2>(double2* p, size_t i, double re, double im) { p[i] = make_double2(re, im); }
 
-__device__ __forceinline__ void block_reduce2(double& a, double& b, double* red) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if ((threadIdx.x & 31) == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
+// Per-rhs reduction inside a CTA for interleaved sets: thread t holds the
+// partial of right-hand side t % R (blockDim is a multiple of R); thread r < R
+// returns the sum over threads r, r + R, ... in that order.
+__device__ __forceinline__ double2 rhs_reduce(double2 v, int R, double2* red) {
+  red[threadIdx.x] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    a = b = 0;
-    for (int k = 0; k < nw; k++) { a += red[2 * k]; b += red[2 * k + 1]; }
-  }
+  double2 s = make_double2(0, 0);
+  if ((int)threadIdx.x < R)
+    for (int m = threadIdx.x; m < (int)blockDim.x; m += R) { s.x += red[m].x; s.y += red[m].y; }
   __syncthreads();
+  return s;
 }
 
-// partial[cta] = sum over this CTA's grid-stride elements of conj(a) b
-template <typename TA, typename TB>
-__global__ void k_dot_partial(const TA* __restrict__ a, const TB* __restrict__ b, size_t n, double2* partial) {
-  __shared__ double red[64];
-  double re = 0, im = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    double2 x = ld2(a, i), y = ld2(b, i);
-    re += x.x * y.x + x.y * y.y;
-    im += x.x * y.y - x.y * y.x;
+// whole-CTA sum (blockDim a multiple of 32), valid in thread 0
+__device__ __forceinline__ double2 cta_reduce(double2 v, double* red) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[2 * w] = v.x; red[2 * w + 1] = v.y; }
+  __syncthreads();
+  double2 s = make_double2(0, 0);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; k++) { s.x += red[2 * k]; s.y += red[2 * k + 1]; }
+  __syncthreads();
+  return s;
+}
+
+// partial[(j*R + r) * G + cta] of <V_j(., r), w(., r)>
+template <typename TV, typename TW, bool INTER>
+__global__ void k_bdots(const TV* __restrict__ V, size_t ldv, int nvec, const TW* __restrict__ w, size_t n, int R,
+                        double2* __restrict__ partial) {
+  __shared__ double2 red[256];
+  const int G = gridDim.x;
+  if (INTER) {
+    const int j = blockIdx.y;
+    const size_t N = n * R, bd = blockDim.x;
+    const size_t chunk = ((N + (size_t)G * bd - 1) / ((size_t)G * bd)) * bd;
+    const size_t beg = (size_t)blockIdx.x * chunk, end = beg + chunk < N ? beg + chunk : N;
+    const TV* vj = V + (size_t)j * ldv;
+    double2 acc = make_double2(0, 0);
+    for (size_t i = beg + threadIdx.x; i < end; i += bd) {
+      double2 x = ld2(vj, i), y = ld2(w, i);
+      acc.x += x.x * y.x + x.y * y.y;
+      acc.y += x.x * y.y - x.y * y.x;
+    }
+    double2 s = rhs_reduce(acc, R, red);
+    if ((int)threadIdx.x < R) partial[((size_t)j * R + threadIdx.x) * G + blockIdx.x] = s;
+  } else {
+    const int jr = blockIdx.y, j = jr / R, r = jr - j * R;
+    const TV* a = V + (size_t)j * ldv + (size_t)r * n;
+    const TW* b = w + (size_t)r * n;
+    double2 acc = make_double2(0, 0);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)G * blockDim.x) {
+      double2 x = ld2(a, i), y = ld2(b, i);
+      acc.x += x.x * y.x + x.y * y.y;
+      acc.y += x.x * y.y - x.y * y.x;
+    }
+    double2 s = cta_reduce(acc, reinterpret_cast<double*>(red));
+    if (threadIdx.x == 0) partial[(size_t)jr * G + blockIdx.x] = s;
   }
-  block_reduce2(re, im, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = make_double2(re, im);
 }
 
 // out[k] = sum_c partial[k * ncta + c], one CTA per k, fixed order
 __global__ void k_reduce_partials(const double2* __restrict__ partial, int ncta, double2* out) {
   __shared__ double red[64];
   const int k = blockIdx.x;
-  double re = 0, im = 0;
+  double2 acc = make_double2(0, 0);
   for (int c = threadIdx.x; c < ncta; c += blockDim.x) {
     double2 v = partial[(size_t)k * ncta + c];
-    re += v.x;
-    im += v.y;
+    acc.x += v.x;
+    acc.y += v.y;
   }
-  block_reduce2(re, im, red);
-  if (threadIdx.x == 0) out[k] = make_double2(re, im);
+  double2 s = cta_reduce(acc, red);
+  if (threadIdx.x == 0) out[k] = s;
 }
 
-// Multi-dot: partial[k][cta] = conj(V_k) . w over one contiguous chunk per CTA,
-// w read once per chunk into shared memory.
-template <typename TV, typename TW>
-__global__ void k_multidot_partial(const TV* __restrict__ V, size_t ldv, int nvec, const TW* __restrict__ w, size_t n,
-                                   double2* partial) {
-  __shared__ double red[64];
-  __shared__ double2 sw[2048];
-  size_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  size_t beg = (size_t)blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
-  for (int k = 0; k < nvec; k++) {
-    double re = 0, im = 0;
-    for (size_t base = beg; base < end; base += 2048) {
-      size_t lim = end - base < 2048 ? end - base : 2048;
-      __syncthreads();
-      for (size_t t = threadIdx.x; t < lim; t += blockDim.x) sw[t] = ld2(w, base + t);
-      __syncthreads();
-      const TV* vk = V + (size_t)k * ldv + base;
-      for (size_t t = threadIdx.x; t < lim; t += blockDim.x) {
-        double2 x = ld2(vk, t), y = sw[t];
-        re += x.x * y.x + x.y * y.y;
-        im += x.x * y.y - x.y * y.x;
-      }
-    }
-    block_reduce2(re, im, red);
-    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = make_double2(re, im);
-  }
-}
-
-// w -= sum_k h[k] V_k     (h complex FP64 on the device)
-template <typename TV, typename TW>
-__global__ void k_multi_axpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ldv, int nvec, const double2* h,
-                             size_t n, double sign) {
-  __shared__ double2 sh[256];
-  for (int k = threadIdx.x; k < nvec; k += blockDim.x) sh[k] = h[k];
+// w(., r) += sign * sum_j coef[j*R + r] V_j(., r); npartial[r * G + cta] = |w(., r)|^2 partials
+template <typename TV, typename TW, bool INTER>
+__global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ldv, int nvec, const double2* __restrict__ coef,
+                         size_t n, int R, double sign, double2* __restrict__ npartial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sc = reinterpret_cast<double2*>(smem_raw);  // coefficients
+  __shared__ double2 red[256];
+  const int G = gridDim.x;
+  const int r_sep = INTER ? 0 : blockIdx.y;
+  const int ncoef = INTER ? nvec * R : nvec;
+  for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = INTER ? coef[k] : coef[(size_t)k * R + r_sep];
   __syncthreads();
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    double2 acc = ld2(w, i);
-    for (int k = 0; k < nvec; k++) {
-      double2 v = ld2(V + (size_t)k * ldv, i), c = sh[k];
-      acc.x += sign * (c.x * v.x - c.y * v.y);
-      acc.y += sign * (c.x * v.y + c.y * v.x);
+  double nn = 0;
+  if (INTER) {
+    const size_t N = n * R, stride = (size_t)G * blockDim.x;  // stride is a multiple of R
+    const int r = threadIdx.x % R;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+      double2 acc = ld2(w, i);
+      for (int j = 0; j < nvec; j++) {
+        double2 v = ld2(V + (size_t)j * ldv, i), c = sc[j * R + r];
+        acc.x += sign * (c.x * v.x - c.y * v.y);
+        acc.y += sign * (c.x * v.y + c.y * v.x);
+      }
+      st2(w, i, acc.x, acc.y);
+      double2 back = ld2(w, i);  // norm of the stored (rounded) vector
+      nn += back.x * back.x + back.y * back.y;
     }
-    st2(w, i, acc.x, acc.y);
+    if (npartial) {
+      double2 s = rhs_reduce(make_double2(nn, 0), R, red);
+      if ((int)threadIdx.x < R) npartial[(size_t)threadIdx.x * G + blockIdx.x] = s;
+    }
+  } else {
+    TW* wr = w + (size_t)r_sep * n;
+    const TV* Vr = V + (size_t)r_sep * n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)G * blockDim.x) {
+      double2 acc = ld2(wr, i);
+      for (int j = 0; j < nvec; j++) {
+        double2 v = ld2(Vr + (size_t)j * ldv, i), c = sc[j];
+        acc.x += sign * (c.x * v.x - c.y * v.y);
+        acc.y += sign * (c.x * v.y + c.y * v.x);
+      }
+      st2(wr, i, acc.x, acc.y);
+      double2 back = ld2(wr, i);
+      nn += back.x * back.x + back.y * back.y;
+    }
+    if (npartial) {
+      double2 s = cta_reduce(make_double2(nn, 0), reinterpret_cast<double*>(red));
+      if (threadIdx.x == 0) npartial[(size_t)r_sep * G + blockIdx.x] = s;
+    }
   }
 }
 
-// y = a x + b y  (a, b complex FP64; x, y may differ in type).  A zero
-// coefficient means the operand is not read at all, so b = 0 assigns y = a x
-// even where y holds uninitialised memory.
-template <typename TX, typename TY>
-__global__ void k_axpby(double2 a, const TX* x, double2 b, TY* y, size_t n) {
-  const bool ra = a.x != 0 || a.y != 0, rb = b.x != 0 || b.y != 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+// y(., r) = a[r] x(., r) + b[r] y(., r); zero coefficients skip their operand
+template <typename TX, typename TY, bool INTER>
+__global__ void k_baxpby(const double2* __restrict__ a, const TX* x, const double2* __restrict__ b, TY* y, size_t n, int R) {
+  const size_t N = n * R;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = INTER ? (int)(i % R) : (int)(i / n);
+    const double2 ca = a[r], cb = b[r];
+    const bool ra = ca.x != 0 || ca.y != 0, rb = cb.x != 0 || cb.y != 0;
     double2 u = ra ? ld2(x, i) : make_double2(0, 0), v = rb ? ld2(y, i) : make_double2(0, 0);
-    double re = a.x * u.x - a.y * u.y + b.x * v.x - b.y * v.y;
-    double im = a.x * u.y + a.y * u.x + b.x * v.y + b.y * v.x;
+    double re = ca.x * u.x - ca.y * u.y + cb.x * v.x - cb.y * v.y;
+    double im = ca.x * u.y + ca.y * u.x + cb.x * v.y + cb.y * v.x;
     st2(y, i, re, im);
   }
 }
@@ -135,67 +175,161 @@ __global__ void k_field_convert(Spinor<PO> out, Spinor<PI> in, long V) {
   out.store(blk, loc, b);
 }
 
-static unsigned stream_grid(size_t n) {
-  size_t g = (n + 255) / 256;
-  return (unsigned)(g < 8192 ? (g ? g : 1) : 8192);
+// ---- host side -------------------------------------------------------------------------
+static int lcm32(int R) {
+  int a = R, b = 32;
+  while (b) { int t = a % b; a = b; b = t; }
+  return R / a * 32;
+}
+// CTA size for interleaved sets: a multiple of both R and 32, at most 256
+static int inter_block(int R) {
+  int l = lcm32(R);
+  if (l > 256) throw Error(DDTM_ERR_ARG, "internal: batch of " + std::to_string(R) + " right-hand sides not supported");
+  return (256 / l) * l;
+}
+static int grid_for(size_t work, int bd, int cap) {
+  size_t g = (work + (size_t)bd * 4 - 1) / ((size_t)bd * 4);
+  return (int)(g < 1 ? 1 : (g > (size_t)cap ? cap : g));
 }
 
-// ---- host wrappers ---------------------------------------------------------------
-Blas::Blas(cudaStream_t s, ScratchPool* pool) : st(s), pool(pool) {}
+CoefRing::~CoefRing() {
+  for (int i = 0; i < SLOTS; i++)
+    if (ev_used[i]) cudaEventDestroy(ev[i]);
+  if (host) cudaFreeHost(host);
+}
 
-void Blas::dots(const void* V, int tv, size_t ldv, int nvec, const void* w, int tw, size_t n, double2* out_host) {
-  ScopedTimer timer_("blas_dots", st);
-  int grid = RED_GRID;
-  double2* partial = (double2*)pool->get("blas_partial", (size_t)nvec * grid * sizeof(double2));
-  double2* dres = (double2*)pool->get("blas_result", (size_t)nvec * sizeof(double2));
-  if (nvec == 1) {
-    if (tv == 1 && tw == 1) k_dot_partial<float2, float2><<<grid, RED_T, 0, st>>>((const float2*)V, (const float2*)w, n, partial);
-    else if (tv == 0 && tw == 0) k_dot_partial<double2, double2><<<grid, RED_T, 0, st>>>((const double2*)V, (const double2*)w, n, partial);
-    else if (tv == 1 && tw == 0) k_dot_partial<float2, double2><<<grid, RED_T, 0, st>>>((const float2*)V, (const double2*)w, n, partial);
-    else k_dot_partial<double2, float2><<<grid, RED_T, 0, st>>>((const double2*)V, (const float2*)w, n, partial);
-  } else {
-    if (tv == 1 && tw == 1) k_multidot_partial<float2, float2><<<grid, RED_T, 0, st>>>((const float2*)V, ldv, nvec, (const float2*)w, n, partial);
-    else if (tv == 0 && tw == 0) k_multidot_partial<double2, double2><<<grid, RED_T, 0, st>>>((const double2*)V, ldv, nvec, (const double2*)w, n, partial);
-    else throw Error(DDTM_ERR_ARG, "internal: mixed multidot");
+const double2* CoefRing::push(const double2* vals, size_t count, cudaStream_t st) {
+  if (!host) {
+    slot_elems = 8192;
+    CK(cudaMallocHost(&host, SLOTS * slot_elems * sizeof(double2)));
+    dev.ensure(SLOTS * slot_elems * sizeof(double2));
   }
-  CKL("dot_partial");
-  k_reduce_partials<<<nvec, RED_T, 0, st>>>(partial, grid, dres);
+  if (count > slot_elems) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");
+  int s = next;
+  next = (next + 1) % SLOTS;
+  if (ev_used[s]) CK(cudaEventSynchronize(ev[s]));
+  else {
+    CK(cudaEventCreateWithFlags(&ev[s], cudaEventDisableTiming));
+    ev_used[s] = true;
+  }
+  memcpy(host + s * slot_elems, vals, count * sizeof(double2));
+  double2* d = dev.as<double2>() + s * slot_elems;
+  CK(cudaMemcpyAsync(d, host + s * slot_elems, count * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(ev[s], st));
+  return d;
+}
+
+Blas::Blas(cudaStream_t s, ScratchPool* p, CoefRing* r) : st(s), pool(p), ring(r) {}
+
+static const double2* coef_to_device(Blas* b, const double2* vals, size_t count, const char* name) {
+  if (b->ring) return b->ring->push(vals, count, b->st);
+  double2* d = (double2*)b->pool->get(name, count * sizeof(double2));
+  CK(cudaMemcpyAsync(d, vals, count * sizeof(double2), cudaMemcpyHostToDevice, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  return d;
+}
+
+#define DISPATCH_TYPES(TV, TW, CALL)                                                 \
+  do {                                                                               \
+    if ((TV) == 1 && (TW) == 1) { typedef float2 A; typedef float2 B; CALL; }        \
+    else if ((TV) == 0 && (TW) == 0) { typedef double2 A; typedef double2 B; CALL; } \
+    else if ((TV) == 1 && (TW) == 0) { typedef float2 A; typedef double2 B; CALL; }  \
+    else { typedef double2 A; typedef float2 B; CALL; }                              \
+  } while (0)
+
+void Blas::dots(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_host) {
+  ScopedTimer timer_("blas_dots", st);
+  const int R = w.R;
+  if (nvec <= 0) return;
+  int bd = w.inter ? inter_block(R) : 256;
+  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  double2* partial = (double2*)pool->get("blas_partial", (size_t)nvec * R * G * sizeof(double2));
+  double2* dres = (double2*)pool->get("blas_result", (size_t)nvec * R * sizeof(double2));
+  dim3 grid(G, w.inter ? nvec : nvec * R);
+  if (grid.y > 65535) throw Error(DDTM_ERR_ARG, "internal: too many vectors in one inner-product batch");
+  if (w.inter)
+    DISPATCH_TYPES(V.type, w.type,
+                   (k_bdots<A, B, true><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
+  else
+    DISPATCH_TYPES(V.type, w.type,
+                   (k_bdots<A, B, false><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
+  CKL("bdots");
+  k_reduce_partials<<<nvec * R, 128, 0, st>>>(partial, G, dres);
   CKL("reduce_partials");
-  CK(cudaMemcpyAsync(out_host, dres, nvec * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(out_host, dres, (size_t)nvec * R * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+}
+
+void Blas::norms2(const VSet& a, double* out_host) {
+  std::vector<double2> t(a.R);
+  dots(a, 0, 1, a, t.data());
+  for (int r = 0; r < a.R; r++) out_host[r] = t[r].x;
+}
+
+template <typename A, typename B, bool INTER>
+static void maxpy_launch(dim3 grid, int bd, size_t smem, cudaStream_t st, B* w, const A* V, size_t ldv, int nvec,
+                         const double2* dc, size_t n, int R, double sign, double2* npart) {
+  static bool cfg = false;
+  if (!cfg) {
+    CK(cudaFuncSetAttribute(k_bmaxpy<A, B, INTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    cfg = true;
+  }
+  k_bmaxpy<A, B, INTER><<<grid, bd, smem, st>>>(w, V, ldv, nvec, dc, n, R, sign, npart);
+}
+
+void Blas::maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_host, double sign,
+                 double* norms2_host) {
+  ScopedTimer timer_("blas_maxpy", st);
+  const int R = w.R;
+  int bd = w.inter ? inter_block(R) : 256;
+  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  const double2* dc = coef_to_device(this, coef_host, (size_t)nvec * R, "blas_coef");
+  double2* npart = norms2_host ? (double2*)pool->get("blas_npartial", (size_t)R * G * sizeof(double2)) : nullptr;
+  size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
+  if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");
+  dim3 grid(G, w.inter ? 1 : R);
+  if (w.inter)
+    DISPATCH_TYPES(V.type, w.type,
+                   (maxpy_launch<A, B, true>(grid, bd, smem, st, (B*)w.p, (const A*)V.p, ldv, nvec, dc, w.n, R, sign, npart)));
+  else
+    DISPATCH_TYPES(V.type, w.type,
+                   (maxpy_launch<A, B, false>(grid, bd, smem, st, (B*)w.p, (const A*)V.p, ldv, nvec, dc, w.n, R, sign, npart)));
+  CKL("bmaxpy");
+  if (norms2_host) {
+    double2* dres = (double2*)pool->get("blas_nresult", (size_t)R * sizeof(double2));
+    k_reduce_partials<<<R, 128, 0, st>>>(npart, G, dres);
+    CKL("reduce_partials");
+    std::vector<double2> t(R);
+    CK(cudaMemcpyAsync(t.data(), dres, (size_t)R * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; r++) norms2_host[r] = t[r].x;
+  }
+}
+
+void Blas::axpby(const double2* a_host, const VSet& x, const double2* b_host, const VSet& y) {
+  ScopedTimer timer_("blas_axpby", st);
+  const int R = y.R;
+  std::vector<double2> ab(2 * (size_t)R);
+  for (int r = 0; r < R; r++) { ab[r] = a_host[r]; ab[R + r] = b_host[r]; }
+  const double2* d = coef_to_device(this, ab.data(), 2 * (size_t)R, "blas_ab");
+  size_t N = y.n * R;
+  size_t g = (N + 255) / 256;
+  unsigned grid = (unsigned)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+  if (y.inter)
+    DISPATCH_TYPES(x.type, y.type, (k_baxpby<A, B, true><<<grid, 256, 0, st>>>(d, (const A*)x.p, d + R, (B*)y.p, y.n, R)));
+  else
+    DISPATCH_TYPES(x.type, y.type, (k_baxpby<A, B, false><<<grid, 256, 0, st>>>(d, (const A*)x.p, d + R, (B*)y.p, y.n, R)));
+  CKL("baxpby");
 }
 
 double Blas::norm2(const void* a, int t, size_t n) {
-  double2 r;
-  dots(a, t, 0, 1, a, t, n, &r);
-  return r.x;
-}
-
-void Blas::multi_axpy(void* w, int tw, const void* V, int tv, size_t ldv, int nvec, const double2* h_host, size_t n,
-                      double sign) {
-  ScopedTimer timer_("blas_multi_axpy", st);
-  if (nvec <= 0) return;
-  if (nvec > 256) throw Error(DDTM_ERR_ARG, "internal: multi_axpy limited to 256 vectors");
-  double2* dh = (double2*)pool->get("blas_coef", 256 * sizeof(double2));
-  CK(cudaMemcpyAsync(dh, h_host, nvec * sizeof(double2), cudaMemcpyHostToDevice, st));
-  unsigned grid = stream_grid(n);
-  if (tw == 1 && tv == 1) k_multi_axpy<float2, float2><<<grid, 256, 0, st>>>((float2*)w, (const float2*)V, ldv, nvec, dh, n, sign);
-  else if (tw == 0 && tv == 0) k_multi_axpy<double2, double2><<<grid, 256, 0, st>>>((double2*)w, (const double2*)V, ldv, nvec, dh, n, sign);
-  else if (tw == 0 && tv == 1) k_multi_axpy<float2, double2><<<grid, 256, 0, st>>>((double2*)w, (const float2*)V, ldv, nvec, dh, n, sign);
-  else k_multi_axpy<double2, float2><<<grid, 256, 0, st>>>((float2*)w, (const double2*)V, ldv, nvec, dh, n, sign);
-  CKL("multi_axpy");
-  // the coefficient buffer is reused by the next call: keep host and device ordered
-  CK(cudaStreamSynchronize(st));
+  double r;
+  norms2(VSet{(void*)a, t, n, 1, true}, &r);
+  return r;
 }
 
 void Blas::axpby(double2 a, const void* x, int tx, double2 b, void* y, int ty, size_t n) {
-  ScopedTimer timer_("blas_axpby", st);
-  unsigned grid = stream_grid(n);
-  if (tx == 1 && ty == 1) k_axpby<float2, float2><<<grid, 256, 0, st>>>(a, (const float2*)x, b, (float2*)y, n);
-  else if (tx == 0 && ty == 0) k_axpby<double2, double2><<<grid, 256, 0, st>>>(a, (const double2*)x, b, (double2*)y, n);
-  else if (tx == 1 && ty == 0) k_axpby<float2, double2><<<grid, 256, 0, st>>>(a, (const float2*)x, b, (double2*)y, n);
-  else k_axpby<double2, float2><<<grid, 256, 0, st>>>(a, (const double2*)x, b, (float2*)y, n);
-  CKL("axpby");
+  axpby(&a, VSet{(void*)x, tx, n, 1, true}, &b, VSet{y, ty, n, 1, true});
 }
 
 void launch_field_convert(const FineGeom& g, int pin, const void* in, const float* inn, int pout, void* out, float* outn,

@@ -1,24 +1,47 @@
-// Host interface of the Krylov vector kernels (blas.cu).  Type tags: 0 =
-// double2 (FP64 complex), 1 = float2 (FP32 complex).  Lengths n count complex
-// elements; ldv is the distance in elements between consecutive vectors of a
-// basis.  Results that come back to the host synchronise the stream.
+// Host interface of the Krylov vector kernels (blas.cu).
+//
+// A "vector set" holds R right-hand sides of n complex entries each, either
+// interleaved (element (e, r) at e * R + r: coarse vectors) or separate
+// (element (e, r) at r * n + e: fine fields).  Type tags: 0 = double2 (FP64
+// complex), 1 = float2 (FP32 complex).  A basis of nvec sets lies at V + j*ldv
+// (ldv in complex elements).  Every inner product accumulates in FP64 and is
+// reduced in a fixed order (deterministic).  Results that come back to the
+// host synchronise the stream; coefficients travel through a pinned ring of
+// buffers guarded by events, so no call blocks on a copy.
 #pragma once
+
+#include <vector>
 
 #include "ddtm_internal.h"
 
 namespace ddtm {
 
+struct VSet {
+  void* p;
+  int type;     // 0 double2, 1 float2
+  size_t n;     // complex entries per right-hand side
+  int R;        // right-hand sides
+  bool inter;   // interleaved (true) or separate (false)
+};
+
 struct Blas {
   cudaStream_t st;
   ScratchPool* pool;
-  Blas(cudaStream_t s, ScratchPool* pool);
-  // out[k] = <V_k, w> = sum conj(V_k) w for k < nvec (FP64 accumulation)
-  void dots(const void* V, int tv, size_t ldv, int nvec, const void* w, int tw, size_t n, double2* out_host);
+  CoefRing* ring;
+  Blas(cudaStream_t s, ScratchPool* pool, CoefRing* ring = nullptr);
+  // out[j * R + r] = <V_j(., r), w(., r)> for j < nvec (host result)
+  void dots(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_host);
+  // per-rhs squared norms (host result)
+  void norms2(const VSet& a, double* out_host);
+  // w(., r) += sign * sum_j coef[j * R + r] V_j(., r); with norms2_host != null
+  // also returns ||w(., r)||^2 of the result
+  void maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_host, double sign,
+             double* norms2_host);
+  // y(., r) = a[r] x(., r) + b[r] y(., r); a zero coefficient skips reading its operand
+  void axpby(const double2* a_host, const VSet& x, const double2* b_host, const VSet& y);
+
+  // single-vector conveniences (R = 1)
   double norm2(const void* a, int t, size_t n);
-  // w += sign * sum_k h[k] V_k
-  void multi_axpy(void* w, int tw, const void* V, int tv, size_t ldv, int nvec, const double2* h_host, size_t n,
-                  double sign);
-  // y = a x + b y
   void axpby(double2 a, const void* x, int tx, double2 b, void* y, int ty, size_t n);
 };
 

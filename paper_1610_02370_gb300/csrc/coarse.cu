@@ -152,90 +152,132 @@ void build_faces(const FineGeom& g, FaceDev& faces) {
 }
 
 // ---- coarse stencil ---------------------------------------------------------------
-// Threads: n per site, SPB sites per CTA; thread (q, r) computes row r of
-// output slot idx = blockIdx.x * SPB + q, whose lattice site is osite[idx]
-// (idx itself when osite == nullptr).  The self term reads x_self[idx], the
-// hop d reads x_hop[tab[(d-1) * nout + idx]]; with full-lattice vectors
-// osite = nullptr and tab = the full neighbour table, with parity-compact
-// vectors tab maps into the compact vector of the other parity.
+// Coarse vectors of a batch of R right-hand sides are stored interleaved,
+// v[(idx * n + k) * R + r], so the R values of one dof are contiguous.  A
+// thread owns one row r of one site and RC consecutive right-hand sides
+// (register blocking: each matrix entry read from HBM is used RC times by the
+// thread and R / RC times by the site's threads); threads of a site are
+// ordered row fastest, so a warp reads consecutive entries of a column-major
+// block.  Output slot idx has lattice site osite[idx] (idx itself when
+// osite == nullptr); the self term reads x_self[idx], hop d reads
+// x_hop[tab[(d-1) * nout + idx]] (tab: full neighbour table for full-lattice
+// vectors, or the parity-compact table into the other parity's vector).
 //   mode & 1: self block + twist i mu_c Gamma5_c;  mode & 2: the 8 hops
-//   y[idx] = sy * y[idx] + sres * result   (sy = 0 overwrites)
-template <typename DS>
+//   y[idx] = sy * y[idx] + sres * result   (sy = 0 overwrites y)
+template <int RC>
+__device__ __forceinline__ void load_rc(const cplx<float>* p, cplx<float> v[RC]) {
+  if (RC == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    float4 a = q[0], b = q[1];
+    v[0] = cplx<float>(a.x, a.y); v[1] = cplx<float>(a.z, a.w);
+    v[2] = cplx<float>(b.x, b.y); v[3] = cplx<float>(b.z, b.w);
+  } else {
+#pragma unroll
+    for (int c = 0; c < RC; c++) v[c] = p[c];
+  }
+}
+
+template <typename DS, int RC>
+__device__ __forceinline__ void block_mv(const DS* A, const cplx<float>* v, int n, int R, cplx<float> acc[RC]) {
+#pragma unroll 4
+  for (int k = 0; k < n; k++) {
+    cplx<float> a = ldD<DS>(A + (size_t)k * n);
+    cplx<float> x[RC];
+    load_rc<RC>(v + (size_t)k * R, x);
+#pragma unroll
+    for (int c = 0; c < RC; c++) cmac(acc[c], a, x[c]);
+  }
+}
+
+template <typename DS, int RC>
 __global__ void k_coarse_apply(cplx<float>* __restrict__ y, const cplx<float>* __restrict__ x_self,
                                const cplx<float>* __restrict__ x_hop, const DS* __restrict__ Dc, const int* __restrict__ tab,
-                               const int* __restrict__ osite, int nout, int n, int nv, float mu_c, int mode, float sres,
-                               float sy) {
-  const int spb = blockDim.x / n;
-  const int q = threadIdx.x / n, r = threadIdx.x - q * n;
+                               const int* __restrict__ osite, int nout, int n, int nv, int R, float mu_c, int mode,
+                               float sres, float sy) {
+  const int nch = R / RC, per = n * nch, spb = blockDim.x / per;
+  const int t = threadIdx.x, r = t % n, ch = (t / n) % nch, q = t / per;
   const int idx = blockIdx.x * spb + q;
   if (q >= spb || idx >= nout) return;
   const int site = osite ? osite[idx] : idx;
-  cplx<float> acc(0, 0);
+  const int c0 = ch * RC;
+  cplx<float> acc[RC];
+#pragma unroll
+  for (int c = 0; c < RC; c++) acc[c] = cplx<float>(0, 0);
   if (mode & 1) {
-    const DS* A = Dc + (size_t)site * 9 * n * n + r;
-    const cplx<float>* v = x_self + (size_t)idx * n;
-#pragma unroll 4
-    for (int k = 0; k < n; k++) cmac(acc, ldD<DS>(A + (size_t)k * n), v[k]);
+    block_mv<DS, RC>(Dc + (size_t)site * 9 * n * n + r, x_self + (size_t)idx * n * R + c0, n, R, acc);
     float m = r < nv ? mu_c : -mu_c;
-    acc = acc + m * times_i(v[r]);
+    cplx<float> xv[RC];
+    load_rc<RC>(x_self + ((size_t)idx * n + r) * R + c0, xv);
+#pragma unroll
+    for (int c = 0; c < RC; c++) acc[c] = acc[c] + m * times_i(xv[c]);
   }
   if (mode & 2)
     for (int d = 1; d < 9; d++) {
       const int src = __ldg(tab + (size_t)(d - 1) * nout + idx);
-      const DS* A = Dc + ((size_t)site * 9 + d) * n * n + r;
-      const cplx<float>* v = x_hop + (size_t)src * n;
-#pragma unroll 4
-      for (int k = 0; k < n; k++) cmac(acc, ldD<DS>(A + (size_t)k * n), v[k]);
+      block_mv<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r, x_hop + (size_t)src * n * R + c0, n, R, acc);
     }
-  size_t o = (size_t)idx * n + r;
-  cplx<float> res = sres * acc;
-  y[o] = sy == 0.f ? res : sy * y[o] + res;
+  cplx<float>* yo = y + ((size_t)idx * n + r) * R + c0;
+#pragma unroll
+  for (int c = 0; c < RC; c++) {
+    cplx<float> res = sres * acc[c];
+    yo[c] = sy == 0.f ? res : sy * yo[c] + res;
+  }
 }
 
 // t[e] = Dinv_e (sr * rhs[e] + sh * hops(v)) on the even sites (compact even
-// output, v compact odd); rhs or v may be null.  Hop and inverse are fused.
-template <typename DS>
+// output, v compact odd); rhs or v may be null.  Hop and inverse are fused:
+// the hop result of a site goes through shared memory to the threads of the
+// same site for the dense matvec with the inverse.
+template <typename DS, int RC>
 __global__ void k_coarse_even(cplx<float>* __restrict__ t, const cplx<float>* __restrict__ rhs, const cplx<float>* __restrict__ v,
                               const DS* __restrict__ Dc, const float2* __restrict__ Dinv, const int* __restrict__ tab,
-                              const int* __restrict__ even, int ne, int n, float sr, float sh) {
+                              const int* __restrict__ even, int ne, int n, int R, float sr, float sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int spb = blockDim.x / n;
-  cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem_raw);
-  const int q = threadIdx.x / n, r = threadIdx.x - q * n;
+  const int nch = R / RC, per = n * nch, spb = blockDim.x / per;
+  cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem_raw);  // [spb][n][R]
+  const int th = threadIdx.x, r = th % n, ch = (th / n) % nch, q = th / per;
   const int e = blockIdx.x * spb + q;
   const bool act = q < spb && e < ne;
+  const int c0 = ch * RC;
   if (act) {
     const int site = even[e];
-    cplx<float> acc(0, 0);
+    cplx<float> acc[RC];
+#pragma unroll
+    for (int c = 0; c < RC; c++) acc[c] = cplx<float>(0, 0);
     if (v)
       for (int d = 1; d < 9; d++) {
         const int src = __ldg(tab + (size_t)(d - 1) * ne + e);
-        const DS* A = Dc + ((size_t)site * 9 + d) * n * n + r;
-        const cplx<float>* vv = v + (size_t)src * n;
-#pragma unroll 4
-        for (int k = 0; k < n; k++) cmac(acc, ldD<DS>(A + (size_t)k * n), vv[k]);
+        block_mv<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r, v + (size_t)src * n * R + c0, n, R, acc);
       }
-    acc = sh * acc;
-    if (rhs) acc = acc + sr * rhs[(size_t)e * n + r];
-    hs[q * n + r] = acc;
+    cplx<float> rv[RC];
+    if (rhs) load_rc<RC>(rhs + ((size_t)e * n + r) * R + c0, rv);
+#pragma unroll
+    for (int c = 0; c < RC; c++) {
+      cplx<float> a = sh * acc[c];
+      if (rhs) a = a + sr * rv[c];
+      hs[((size_t)q * n + r) * R + c0 + c] = a;
+    }
   }
   __syncthreads();
   if (act) {
-    cplx<float> out(0, 0);
-    const float2* Mi = Dinv + (size_t)e * n * n + r;
-#pragma unroll 4
-    for (int k = 0; k < n; k++) cmac(out, ld(Mi + (size_t)k * n), hs[q * n + k]);
-    t[(size_t)e * n + r] = out;
+    cplx<float> out[RC];
+#pragma unroll
+    for (int c = 0; c < RC; c++) out[c] = cplx<float>(0, 0);
+    block_mv<float2, RC>(Dinv + (size_t)e * n * n + r, hs + (size_t)q * n * R + c0, n, R, out);
+    cplx<float>* to = t + ((size_t)e * n + r) * R + c0;
+#pragma unroll
+    for (int c = 0; c < RC; c++) to[c] = out[c];
   }
 }
 
-// gather (dir = 0: compact[i] = full[list[i]]) or scatter (dir = 1)
+// gather (dir = 0: compact[i] = full[list[i]]) or scatter (dir = 1), n*R
+// contiguous complex numbers per site
 __global__ void k_parity_copy(cplx<float>* __restrict__ compact, cplx<float>* __restrict__ full, const int* __restrict__ list,
-                              int cnt, int n, int dir) {
+                              int cnt, int nr, int dir) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)cnt * n) return;
-  int i = (int)(t / n), r = (int)(t - (size_t)i * n);
-  size_t f = (size_t)list[i] * n + r;
+  if (t >= (size_t)cnt * nr) return;
+  int i = (int)(t / nr), r = (int)(t - (size_t)i * nr);
+  size_t f = (size_t)list[i] * nr + r;
   if (dir == 0) compact[t] = full[f];
   else full[f] = compact[t];
 }
@@ -297,58 +339,81 @@ __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__
     }
 }
 
-static int spb_for(int n) { return n >= 128 ? 1 : (n >= 64 ? 2 : 4); }
+// threads per CTA: whole sites of n * (R / RC) threads, at most 256 per CTA
+static int sites_per_cta(int per) { return per >= 256 ? 1 : 256 / per; }
 
-template <typename DS>
+template <typename DS, int RC>
 static void coarse_apply_t(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
-                           const int* osite, int nout, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  int spb = spb_for(c.n);
+                           const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
+  int per = c.n * (R / RC), spb = sites_per_cta(per);
   unsigned grid = (unsigned)((nout + spb - 1) / spb);
   if (grid == 0) return;
-  k_coarse_apply<DS><<<grid, spb * c.n, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, (float)mu_c, mode,
-                                                 sres, sy);
+  k_coarse_apply<DS, RC><<<grid, spb * per, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, R, (float)mu_c,
+                                                     mode, sres, sy);
   CKL("coarse_apply");
 }
 
-void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, double mu_c, int mode, float sres,
-                              float sy, cudaStream_t st) {
-  ScopedTimer timer_("coarse_apply", st);
-  if (c.prec == PREC_F16) coarse_apply_t<__half2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, mu_c, mode, sres, sy, st);
-  else coarse_apply_t<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, mu_c, mode, sres, sy, st);
+template <typename DS>
+static void coarse_apply_d(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
+                           const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
+  if (R % 4 == 0) coarse_apply_t<DS, 4>(c, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
+  else coarse_apply_t<DS, 1>(c, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
 }
 
-void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e,
+void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,
+                              float sres, float sy, cudaStream_t st) {
+  ScopedTimer timer_("coarse_apply", st);
+  if (c.prec == PREC_F16) coarse_apply_d<__half2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, mu_c, mode, sres, sy, st);
+  else coarse_apply_d<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, mu_c, mode, sres, sy, st);
+}
+
+void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e, int R,
                              double mu_c, int mode, float sres, float sy, cudaStream_t st) {
   ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_apply_odd_f16" : "coarse_apply_odd_f32", st);
   int no = (int)c.h_odd.size();
   if (c.prec == PREC_F16)
-    coarse_apply_t<__half2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, mu_c, mode, sres, sy, st);
+    coarse_apply_d<__half2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, R, mu_c, mode, sres, sy, st);
   else
-    coarse_apply_t<float2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, mu_c, mode, sres, sy, st);
+    coarse_apply_d<float2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, R, mu_c, mode, sres, sy, st);
 }
 
-void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, float sr,
-                        float sh, cudaStream_t st) {
-  ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_even_f16" : "coarse_even_f32", st);
-  int spb = spb_for(c.n);
+template <typename DS, int RC>
+static void coarse_even_t(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
+                          float sh, cudaStream_t st) {
+  int per = c.n * (R / RC), spb = sites_per_cta(per);
   int ne = (int)c.h_even.size();
   unsigned grid = (unsigned)((ne + spb - 1) / spb);
-  size_t smem = (size_t)spb * c.n * sizeof(cplx<float>);
-  if (c.prec == PREC_F16)
-    k_coarse_even<__half2><<<grid, spb * c.n, smem, st>>>(t, rhs, v, c.Dc.as<__half2>(), c.Dinv.as<float2>(),
-                                                          c.nbr_eo.as<int>(), c.even.as<int>(), ne, c.n, sr, sh);
-  else
-    k_coarse_even<float2><<<grid, spb * c.n, smem, st>>>(t, rhs, v, c.Dc.as<float2>(), c.Dinv.as<float2>(),
-                                                         c.nbr_eo.as<int>(), c.even.as<int>(), ne, c.n, sr, sh);
+  if (grid == 0) return;
+  size_t smem = (size_t)spb * c.n * R * sizeof(cplx<float>);
+  static bool cfg = false;
+  if (!cfg) {
+    CK(cudaFuncSetAttribute(k_coarse_even<DS, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    cfg = true;
+  }
+  k_coarse_even<DS, RC><<<grid, spb * per, smem, st>>>(t, rhs, v, c.Dc.as<DS>(), c.Dinv.as<float2>(), c.nbr_eo.as<int>(),
+                                                       c.even.as<int>(), ne, c.n, R, sr, sh);
   CKL("coarse_even");
 }
 
-void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int dir, cudaStream_t st) {
+void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
+                        float sh, cudaStream_t st) {
+  ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_even_f16" : "coarse_even_f32", st);
+  if (c.prec == PREC_F16) {
+    if (R % 4 == 0) coarse_even_t<__half2, 4>(c, t, rhs, v, R, sr, sh, st);
+    else coarse_even_t<__half2, 1>(c, t, rhs, v, R, sr, sh, st);
+  } else {
+    if (R % 4 == 0) coarse_even_t<float2, 4>(c, t, rhs, v, R, sr, sh, st);
+    else coarse_even_t<float2, 1>(c, t, rhs, v, R, sr, sh, st);
+  }
+}
+
+void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int R, int dir,
+                        cudaStream_t st) {
   ScopedTimer timer_("parity_copy", st);
   int cnt = parity == 0 ? (int)c.h_even.size() : (int)c.h_odd.size();
   const int* list = parity == 0 ? c.even.as<int>() : c.odd.as<int>();
-  size_t tot = (size_t)cnt * c.n;
-  k_parity_copy<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(compact, full, list, cnt, c.n, dir);
+  size_t tot = (size_t)cnt * c.n * R;
+  k_parity_copy<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(compact, full, list, cnt, c.n * R, dir);
   CKL("parity_copy");
 }
 

@@ -77,6 +77,24 @@ struct FaceDev {
   int off[9] = {0};
 };
 
+// Pinned host ring of coefficient blocks copied to the device asynchronously;
+// each slot carries an event so a slot is reused only after its copy is done.
+struct CoefRing {
+  static const int SLOTS = 64;
+  size_t slot_elems = 0;
+  double2* host = nullptr;
+  DevBuf dev;
+  cudaEvent_t ev[SLOTS];
+  bool ev_used[SLOTS] = {false};
+  int next = 0;
+  CoefRing() {}
+  CoefRing(const CoefRing&) = delete;
+  CoefRing& operator=(const CoefRing&) = delete;
+  ~CoefRing();
+  // copy count values to a device slot (asynchronously on st) and return it
+  const double2* push(const double2* vals, size_t count, cudaStream_t st);
+};
+
 struct ScratchPool {
   std::map<std::string, DevBuf*> bufs;
   ~ScratchPool();
@@ -116,6 +134,7 @@ struct ddtm_ctx {
   ddtm::CoarseLevel c1;
   bool c1_geom = false;
   long coarse_iters = 0;   // accumulated by the coarsest solves
+  ddtm::CoefRing ring;     // coefficient transfers of the Krylov solvers
   bool have_P = false;
   bool setup_done = false;
   double setup_mu = 0;
@@ -148,6 +167,6 @@ void launch_dslash(const FineGeom& g, int prec, void* y, float* ynrm, const void
 // ---- sap.cu ----------------------------------------------------------------------
 void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,
                      const void* clover, const void* sinv, const int* blocks, const int* zero_blocks, int nblocks,
-                     int zero_x, int nmr, double mu, cudaStream_t s);
+                     int zero_x, int nmr, double mu, int nrhs, cudaStream_t s);
 
 }  // namespace ddtm

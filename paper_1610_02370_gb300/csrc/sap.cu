@@ -28,6 +28,8 @@ struct SapArgs {
   int zero_x;              // x is implicitly zero on entry
   int nmr;
   R mu;
+  size_t fstride;          // store2 elements between right-hand sides (12 V)
+  long V;                  // sites (stride of the FP16 scales between right-hand sides)
 };
 
 // sum over the CTA of three reals; every thread receives the totals
@@ -65,7 +67,13 @@ __global__ void k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, Si
   Z* eo = re + 12 * Vh;                     // odd sites: correction e_o
   R* red = reinterpret_cast<R*>(eo + 12 * Vh);
 
-  const int blk = a.blocks[blockIdx.x];
+  // grid: x = right-hand side, y = block of this colour
+  const int rhs = blockIdx.x;
+  x.d += (size_t)rhs * a.fstride;
+  b.d += (size_t)rhs * a.fstride;
+  if (x.nrm) x.nrm += (size_t)rhs * a.V;
+  if (b.nrm) b.nrm += (size_t)rhs * a.V;
+  const int blk = a.blocks[blockIdx.y];
   const int i = threadIdx.x;
   const bool act = i < Vh;
   const int le = i, lo = Vh + i;  // this thread's even and odd site
@@ -74,7 +82,7 @@ __global__ void k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, Si
     Z zero[12];
 #pragma unroll
     for (int c = 0; c < 12; c++) zero[c] = Z(0, 0);
-    int zb = a.zero_blocks[blockIdx.x];
+    int zb = a.zero_blocks[blockIdx.y];
     x.store(zb, le, zero);
     x.store(zb, lo, zero);
   }
@@ -196,7 +204,7 @@ int sap_threads(int Vb) {
 template <int P>
 static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void* b, const float* bn, const void* links,
                               const void* clover, const void* sinv, const int* blocks, const int* zero_blocks,
-                              int nblocks, int zero_x, int nmr, double mu, cudaStream_t s) {
+                              int nblocks, int zero_x, int nmr, double mu, int nrhs, cudaStream_t s) {
   typedef typename Prec<P>::store2 S;
   typedef typename Prec<P>::real R;
   Geo q{g.Vb, g.Nb, g.loc_nbr.as<uint32_t>(), g.blk_nbr.as<int>()};
@@ -206,8 +214,9 @@ static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void*
     CK(cudaFuncSetAttribute(k_sap_half<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
-  SapArgs<R> a{blocks, zero_blocks, zero_x, nmr, (R)mu};
-  k_sap_half<P><<<nblocks, sap_threads(g.Vb), smem, s>>>(
+  SapArgs<R> a{blocks, zero_blocks, zero_x, nmr, (R)mu, (size_t)g.V * 12, g.V};
+  dim3 grid(nrhs, nblocks);
+  k_sap_half<P><<<grid, sap_threads(g.Vb), smem, s>>>(
       Spinor<P>{(S*)x, xn, g.Vb}, Spinor<P>{(S*)b, (float*)bn, g.Vb}, Links<P>{(const S*)links, g.Vb},
       Clover<P>{(const S*)clover, g.Vb}, SiteInv<P>{(const S*)sinv, g.Vb / 2}, q, a);
   CKL("sap_half");
@@ -215,14 +224,14 @@ static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void*
 
 void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,
                      const void* clover, const void* sinv, const int* blocks, const int* zero_blocks, int nblocks,
-                     int zero_x, int nmr, double mu, cudaStream_t s) {
+                     int zero_x, int nmr, double mu, int nrhs, cudaStream_t s) {
   ScopedTimer timer_(prec == PREC_F64 ? "sap_half_f64" : prec == PREC_F32 ? "sap_half_f32" : "sap_half_f16", s);
   if (prec == PREC_F64)
-    launch_sap_half_t<PREC_F64>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, s);
+    launch_sap_half_t<PREC_F64>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, nrhs, s);
   else if (prec == PREC_F32)
-    launch_sap_half_t<PREC_F32>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, s);
+    launch_sap_half_t<PREC_F32>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, nrhs, s);
   else
-    launch_sap_half_t<PREC_F16>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, s);
+    launch_sap_half_t<PREC_F16>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, nrhs, s);
 }
 
 }  // namespace ddtm

@@ -48,7 +48,7 @@ void invalidate_setup(ddtm_ctx* c) {
 }
 
 void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const float* bn, double mu, int ncycles, int nmr,
-             bool from_zero) {
+             bool from_zero, int R) {
   ensure_fine_prec(c, prec);
   ensure_site_inverse(c, prec, mu);
   const FineGeom& g = c->g;
@@ -57,21 +57,25 @@ void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const flo
   const int* black = red + half;
   if (ncycles <= 0) {
     if (from_zero) {
-      CK(cudaMemsetAsync(x, 0, (size_t)g.V * 12 * store2_bytes(prec), c->stream));
-      if (xn) CK(cudaMemsetAsync(xn, 0, (size_t)g.V * sizeof(float), c->stream));
+      CK(cudaMemsetAsync(x, 0, (size_t)R * g.V * 12 * store2_bytes(prec), c->stream));
+      if (xn) CK(cudaMemsetAsync(xn, 0, (size_t)R * g.V * sizeof(float), c->stream));
     }
     return;
   }
   for (int cyc = 0; cyc < ncycles; cyc++) {
     launch_sap_half(g, prec, x, xn, b, bn, c->links[prec].p, c->clover[prec].p, c->sinv[prec].p, red, black, half,
-                    from_zero && cyc == 0, nmr, mu, c->stream);
+                    from_zero && cyc == 0, nmr, mu, R, c->stream);
     launch_sap_half(g, prec, x, xn, b, bn, c->links[prec].p, c->clover[prec].p, c->sinv[prec].p, black, red, half, 0,
-                    nmr, mu, c->stream);
+                    nmr, mu, R, c->stream);
   }
 }
 
 // ---- hierarchy -----------------------------------------------------------------------
 static size_t fine_field_bytes(const FineGeom& g, int prec) { return (size_t)g.V * 12 * store2_bytes(prec); }
+
+// coarse batches are padded to a multiple of 4 right-hand sides (register
+// blocking of the coarse kernels); the padding columns carry zeros
+int coarse_batch(int R) { return R == 1 ? 1 : (R + 3) / 4 * 4; }
 
 // P from the current test vectors, then the Galerkin coarse operator
 void build_hierarchy(ddtm_ctx* c) {
@@ -120,240 +124,305 @@ static const void* P_for(ddtm_ctx* c, int prec, int* pprec) {
   return c->P0.p;
 }
 
-// ---- GMRES on FP32 vectors ---------------------------------------------------------------
+// ---- batched GMRES on FP32 vectors --------------------------------------------------------
+// A(out, in) applies the operator to a batch of R interleaved vectors.
 typedef std::function<void(cplx<float>*, const cplx<float>*)> OpF32;
 
-// GMRES(m) with restarts for A x = b (complex FP32 vectors of length L, FP64
-// inner products): classical Gram-Schmidt with one reorthogonalisation,
-// Givens rotations on the host.  x is overwritten (zero start).  Returns the
-// iteration count; *relres the last residual estimate relative to ||b||.
-static int gmres_f32(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float>* b, size_t L, int m, int max_restarts,
-                     double tol, double* relres, const char* tag) {
-  Blas B(c->stream, &c->scratch);
+// Lockstep GMRES(m) with restarts for R systems A x_r = b_r (complex FP32
+// vectors of L entries each, interleaved; FP64 inner products).  Every
+// iteration orthogonalises all R Krylov vectors with one multi-dot and one
+// fused multi-axpy + norm (classical Gram-Schmidt; a second pass when tol is
+// below 1e-3), keeps each system's Hessenberg matrix and Givens rotations on
+// the host, and stops when every system's residual estimate is below tol
+// (systems with b_r = 0 count as solved with x_r = 0).  x is overwritten
+// (zero start).  Returns the iteration count; relres[r] the estimates.
+static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float>* b, size_t L, int R, int m, int max_restarts,
+                   double tol, double* relres, const char* tag) {
+  Blas B(c->stream, &c->scratch, &c->ring);
   std::string t(tag);
-  cplx<float>* V = (cplx<float>*)c->scratch.get(t + "_V", (size_t)(m + 1) * L * sizeof(float2));
-  cplx<float>* w = (cplx<float>*)c->scratch.get(t + "_w", L * sizeof(float2));
-  CK(cudaMemsetAsync(x, 0, L * sizeof(float2), c->stream));
-  double bn = sqrt(B.norm2(b, 1, L));
-  *relres = 0;
-  if (bn == 0) return 0;
-  std::vector<zc> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
-  std::vector<double2> h(m + 1), h2(m + 1);
+  const size_t N = L * R;
+  cplx<float>* V = (cplx<float>*)c->scratch.get(t + "_V", (size_t)(m + 1) * N * sizeof(float2));
+  cplx<float>* w = (cplx<float>*)c->scratch.get(t + "_w", N * sizeof(float2));
+  CK(cudaMemsetAsync(x, 0, N * sizeof(float2), c->stream));
+  auto vs = [&](const void* p) { return VSet{(void*)p, 1, L, R, true}; };
+  std::vector<double> bn(R), beta(R), hn2(R), est(R, 0.0);
+  B.norms2(vs(b), bn.data());
+  for (int r = 0; r < R; r++) bn[r] = sqrt(bn[r]);
+  const bool reorth = tol < 1e-3;
+  std::vector<zc> H((size_t)R * (m + 1) * m), cs((size_t)R * m), sn((size_t)R * m), g((size_t)R * (m + 1));
+  std::vector<double2> h((size_t)(m + 1) * R), h2((size_t)(m + 1) * R), coef(R), zero(R, make_double2(0, 0)),
+      one(R, make_double2(1, 0)), mone(R, make_double2(-1, 0));
+  auto Hat = [&](int r, int i, int j) -> zc& { return H[((size_t)r * (m + 1) + i) * m + j]; };
+  auto all_done = [&]() {
+    for (int r = 0; r < R; r++)
+      if (bn[r] > 0 && !(est[r] <= tol)) return false;
+    return true;
+  };
   int iters = 0;
-  double est = 1;
   for (int cyc = 0; cyc <= max_restarts; cyc++) {
-    // r = b - A x into V_0
     if (cyc == 0) {
-      CK(cudaMemcpyAsync(V, b, L * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(V, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
     } else {
       A(w, x);
-      CK(cudaMemcpyAsync(V, b, L * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
-      B.axpby(make_double2(-1, 0), w, 1, make_double2(1, 0), V, 1, L);
+      CK(cudaMemcpyAsync(V, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+      B.axpby(mone.data(), vs(w), one.data(), vs(V));
     }
-    double beta = sqrt(B.norm2(V, 1, L));
-    est = beta / bn;
-    if (est <= tol || beta == 0) break;
-    B.axpby(make_double2(0, 0), V, 1, make_double2(1.0 / beta, 0), V, 1, L);
+    B.norms2(vs(V), beta.data());
+    for (int r = 0; r < R; r++) {
+      beta[r] = sqrt(beta[r]);
+      est[r] = bn[r] > 0 ? beta[r] / bn[r] : 0.0;
+      if (!std::isfinite(est[r])) throw Error(DDTM_ERR_NAN, "non-finite residual in GMRES (" + t + ")");
+      coef[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
+    }
+    if (all_done()) break;
+    B.axpby(zero.data(), vs(V), coef.data(), vs(V));
     std::fill(g.begin(), g.end(), zc(0));
-    g[0] = beta;
+    for (int r = 0; r < R; r++) g[(size_t)r * (m + 1)] = beta[r];
     int k = 0;
     for (int j = 0; j < m; j++) {
-      A(w, V + (size_t)j * L);
-      B.dots(V, 1, L, j + 1, w, 1, L, h.data());
-      B.multi_axpy(w, 1, V, 1, L, j + 1, h.data(), L, -1.0);
-      B.dots(V, 1, L, j + 1, w, 1, L, h2.data());
-      B.multi_axpy(w, 1, V, 1, L, j + 1, h2.data(), L, -1.0);
-      for (int i = 0; i <= j; i++) H[(size_t)i * m + j] = zc(h[i].x + h2[i].x, h[i].y + h2[i].y);
-      double hn = sqrt(B.norm2(w, 1, L));
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; i++) {
-        zc a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      A(w, V + (size_t)j * N);
+      B.dots(vs(V), N, j + 1, vs(w), h.data());
+      B.maxpy(vs(w), vs(V), N, j + 1, h.data(), -1.0, reorth ? nullptr : hn2.data());
+      if (reorth) {
+        B.dots(vs(V), N, j + 1, vs(w), h2.data());
+        B.maxpy(vs(w), vs(V), N, j + 1, h2.data(), -1.0, hn2.data());
+        for (size_t q = 0; q < h.size(); q++) { h[q].x += h2[q].x; h[q].y += h2[q].y; }
       }
-      zc a = H[(size_t)j * m + j];
-      double rho = sqrt(std::norm(a) + hn * hn);
-      cs[j] = rho > 0 ? a / rho : zc(1);
-      sn[j] = rho > 0 ? zc(hn / rho) : zc(0);
-      H[(size_t)j * m + j] = rho;
-      H[(size_t)(j + 1) * m + j] = 0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = std::conj(cs[j]) * g[j];
+      for (int r = 0; r < R; r++) {
+        double hn = sqrt(hn2[r]);
+        for (int i = 0; i <= j; i++) Hat(r, i, j) = zc(h[(size_t)i * R + r].x, h[(size_t)i * R + r].y);
+        Hat(r, j + 1, j) = hn;
+        for (int i = 0; i < j; i++) {
+          zc a = Hat(r, i, j), bb = Hat(r, i + 1, j);
+          Hat(r, i, j) = std::conj(cs[(size_t)r * m + i]) * a + std::conj(sn[(size_t)r * m + i]) * bb;
+          Hat(r, i + 1, j) = -sn[(size_t)r * m + i] * a + cs[(size_t)r * m + i] * bb;
+        }
+        zc a = Hat(r, j, j);
+        double rho = sqrt(std::norm(a) + hn * hn);
+        cs[(size_t)r * m + j] = rho > 0 ? a / rho : zc(1);
+        sn[(size_t)r * m + j] = rho > 0 ? zc(hn / rho) : zc(0);
+        Hat(r, j, j) = rho;
+        Hat(r, j + 1, j) = 0;
+        zc* gr = &g[(size_t)r * (m + 1)];
+        gr[j + 1] = -sn[(size_t)r * m + j] * gr[j];
+        gr[j] = std::conj(cs[(size_t)r * m + j]) * gr[j];
+        est[r] = bn[r] > 0 ? std::abs(gr[j + 1]) / bn[r] : 0.0;
+        if (!std::isfinite(est[r])) throw Error(DDTM_ERR_NAN, "non-finite residual estimate in GMRES (" + t + ")");
+        coef[r] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0);
+      }
       k = j + 1;
       iters++;
-      est = std::abs(g[j + 1]) / bn;
-      if (est <= tol || hn == 0 || !std::isfinite(est)) break;
-      B.axpby(make_double2(1.0 / hn, 0), w, 1, make_double2(0, 0), V + (size_t)(j + 1) * L, 1, L);  // V_{j+1} = w / hn
+      if (all_done() || j == m - 1) break;
+      B.axpby(coef.data(), vs(w), zero.data(), vs(V + (size_t)(j + 1) * N));  // V_{j+1} = w / hn
     }
-    if (!std::isfinite(est)) throw Error(DDTM_ERR_NAN, "non-finite residual in GMRES (" + t + ")");
-    std::vector<zc> y(k);
-    for (int i = k - 1; i >= 0; i--) {
-      zc s = g[i];
-      for (int l = i + 1; l < k; l++) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
+    // x += V y per system, y from the triangular systems (zero where a pivot vanished)
+    std::vector<double2> yc((size_t)k * R);
+    for (int r = 0; r < R; r++) {
+      std::vector<zc> y(k);
+      for (int i = k - 1; i >= 0; i--) {
+        zc sacc = g[(size_t)r * (m + 1) + i];
+        for (int l = i + 1; l < k; l++) sacc -= Hat(r, i, l) * y[l];
+        zc d = Hat(r, i, i);
+        y[i] = std::abs(d) > 0 ? sacc / d : zc(0);
+      }
+      for (int i = 0; i < k; i++) yc[(size_t)i * R + r] = make_double2(y[i].real(), y[i].imag());
     }
-    std::vector<double2> yd(k);
-    for (int i = 0; i < k; i++) yd[i] = make_double2(y[i].real(), y[i].imag());
-    B.multi_axpy(x, 1, V, 1, L, k, yd.data(), L, +1.0);
-    if (est <= tol) break;
+    B.maxpy(vs(x), vs(V), N, k, yc.data(), +1.0, nullptr);
+    if (all_done()) break;
   }
-  *relres = est;
+  for (int r = 0; r < R; r++) relres[r] = est[r];
   return iters;
 }
 
 // ---- coarsest level: even-odd GMRES (Sec. 2.5) ------------------------------------------
-// D_c(mu_c) phi = eta:  rhat = eta_o - D_oe D_ee^-1 eta_e;  GMRES on
-// D_hat = D_oo - D_oe D_ee^-1 D_eo;  phi_e = D_ee^-1 (eta_e - D_eo phi_o).
-int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full, double mu_c, int restart,
+// D_c(mu_c) phi = eta for a batch of Rc interleaved coarse vectors:
+// rhat = eta_o - D_oe D_ee^-1 eta_e;  GMRES on D_hat = D_oo - D_oe D_ee^-1 D_eo;
+// phi_e = D_ee^-1 (eta_e - D_eo phi_o).  Returns the iteration count; relres
+// receives the per-rhs estimates of the reduced system.
+int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full, int Rc, double mu_c, int restart,
                     int max_restarts, double tol, double* relres) {
   CoarseLevel& L = c->c1;
   if (!L.inv_valid || L.inv_mu != mu_c) launch_self_inverse(L, mu_c, c->stream);
   size_t ne = L.h_even.size(), no = L.h_odd.size(), n = L.n;
-  cplx<float>* be = (cplx<float>*)c->scratch.get("ceo_be", ne * n * 8);
-  cplx<float>* bo = (cplx<float>*)c->scratch.get("ceo_bo", no * n * 8);
-  cplx<float>* te = (cplx<float>*)c->scratch.get("ceo_te", ne * n * 8);
-  cplx<float>* xo = (cplx<float>*)c->scratch.get("ceo_xo", no * n * 8);
-  launch_parity_copy(L, 0, be, (cplx<float>*)b_full, 0, c->stream);
-  launch_parity_copy(L, 1, bo, (cplx<float>*)b_full, 0, c->stream);
-  launch_coarse_even(L, te, be, nullptr, 1.f, 0.f, c->stream);                   // te = D_ee^-1 eta_e
-  launch_coarse_apply_odd(L, bo, nullptr, te, mu_c, 2, -1.f, 1.f, c->stream);     // rhat = eta_o - D_oe te
-  cplx<float>* tA = (cplx<float>*)c->scratch.get("ceo_tA", ne * n * 8);
+  size_t bytes_e = ne * n * Rc * 8, bytes_o = no * n * Rc * 8;
+  cplx<float>* be = (cplx<float>*)c->scratch.get("ceo_be", bytes_e);
+  cplx<float>* bo = (cplx<float>*)c->scratch.get("ceo_bo", bytes_o);
+  cplx<float>* te = (cplx<float>*)c->scratch.get("ceo_te", bytes_e);
+  cplx<float>* xo = (cplx<float>*)c->scratch.get("ceo_xo", bytes_o);
+  cplx<float>* tA = (cplx<float>*)c->scratch.get("ceo_tA", bytes_e);
+  launch_parity_copy(L, 0, be, (cplx<float>*)b_full, Rc, 0, c->stream);
+  launch_parity_copy(L, 1, bo, (cplx<float>*)b_full, Rc, 0, c->stream);
+  launch_coarse_even(L, te, be, nullptr, Rc, 1.f, 0.f, c->stream);                 // te = D_ee^-1 eta_e
+  launch_coarse_apply_odd(L, bo, nullptr, te, Rc, mu_c, 2, -1.f, 1.f, c->stream);   // rhat = eta_o - D_oe te
   OpF32 Dhat = [&](cplx<float>* out, const cplx<float>* in) {
-    launch_coarse_even(L, tA, nullptr, in, 0.f, 1.f, c->stream);                 // tA = D_ee^-1 D_eo in
-    launch_coarse_apply_odd(L, out, in, nullptr, mu_c, 1, 1.f, 0.f, c->stream);  // out = D_oo in
-    launch_coarse_apply_odd(L, out, nullptr, tA, mu_c, 2, -1.f, 1.f, c->stream); // out -= D_oe tA
+    launch_coarse_even(L, tA, nullptr, in, Rc, 0.f, 1.f, c->stream);                 // tA = D_ee^-1 D_eo in
+    launch_coarse_apply_odd(L, out, in, nullptr, Rc, mu_c, 1, 1.f, 0.f, c->stream);  // out = D_oo in
+    launch_coarse_apply_odd(L, out, nullptr, tA, Rc, mu_c, 2, -1.f, 1.f, c->stream); // out -= D_oe tA
   };
-  int it = gmres_f32(c, Dhat, xo, bo, no * n, restart, max_restarts, tol, relres, "cgm");
-  launch_coarse_even(L, te, be, xo, 1.f, -1.f, c->stream);  // phi_e = D_ee^-1 (eta_e - D_eo phi_o)
-  launch_parity_copy(L, 0, te, x_full, 1, c->stream);
-  launch_parity_copy(L, 1, xo, x_full, 1, c->stream);
-  c->coarse_iters += it;
+  int it = gmres_b(c, Dhat, xo, bo, no * n, Rc, restart, max_restarts, tol, relres, "cgm");
+  launch_coarse_even(L, te, be, xo, Rc, 1.f, -1.f, c->stream);  // phi_e = D_ee^-1 (eta_e - D_eo phi_o)
+  launch_parity_copy(L, 0, te, x_full, Rc, 1, c->stream);
+  launch_parity_copy(L, 1, xo, x_full, Rc, 1, c->stream);
+  c->coarse_iters += (long)it * Rc;
   return it;
 }
 
 // ---- K-cycle preconditioner (Sec. 2.2): z = P D_c^-1 R v, then post-smoothing ----------
-void mg_precondition(ddtm_ctx* c, int prec, void* z, float* zn, const void* v, const float* vn, double mu) {
+// R fine fields of precision prec at stride 12 V (FP16 scales at stride V).
+void mg_precondition(ddtm_ctx* c, int prec, void* z, float* zn, const void* v, const float* vn, double mu, int R) {
   const FineGeom& g = c->g;
   CoarseLevel& L = c->c1;
-  size_t nc = (size_t)L.Nc * L.n;
+  const int Rc = coarse_batch(R);
+  size_t nc = (size_t)L.Nc * L.n * Rc;
   cplx<float>* cv = (cplx<float>*)c->scratch.get("mg_c", nc * 8);
   cplx<float>* ev = (cplx<float>*)c->scratch.get("mg_e", nc * 8);
+  if (Rc != R) CK(cudaMemsetAsync(cv, 0, nc * 8, c->stream));
   int pprec;
   const void* P = P_for(c, prec, &pprec);
-  launch_restrict(g, prec, cv, v, vn, P, pprec, L.nv, c->stream);
-  double rr;
-  coarse_eo_solve(c, ev, cv, c->p.delta * mu, c->p.coarse_restart, c->p.coarse_max_restarts, c->p.coarse_tol, &rr);
-  launch_prolong(g, prec, z, zn, ev, P, pprec, L.nv, 0, c->stream);
-  sap_run(c, prec, z, zn, v, vn, mu, c->p.post_smooth, c->p.nmr, false);
+  launch_restrict(g, prec, cv, v, vn, P, pprec, L.nv, R, Rc, c->stream);
+  std::vector<double> rr(Rc);
+  coarse_eo_solve(c, ev, cv, Rc, c->p.delta * mu, c->p.coarse_restart, c->p.coarse_max_restarts, c->p.coarse_tol,
+                  rr.data());
+  launch_prolong(g, prec, z, zn, ev, P, pprec, L.nv, R, Rc, 0, c->stream);
+  sap_run(c, prec, z, zn, v, vn, mu, c->p.post_smooth, c->p.nmr, false, R);
 }
 
 // ---- outer flexible GMRES in FP64 (Sec. 2.5) --------------------------------------------
-// Arnoldi basis V and all orthogonalisation in FP64; Z_j = M v_j stored in the
+// R systems in lockstep.  The Arnoldi basis V and all orthogonalisation are
+// FP64 (classical Gram-Schmidt, two passes); Z_j = M v_j is stored in the
 // smoother precision (a flexible method takes Z_j as it is: w = D Z_j is
 // applied to exactly the stored Z_j, and x is updated with the same Z_j).  A
-// cycle ends at the restart length or when its residual estimate drops below
-// restart_tol times the cycle's starting residual (Table 1: mixed-precision
-// restart criterion) or below the target; every cycle starts from the true
-// FP64 residual b - D x.
+// cycle ends at the restart length, when every residual estimate is below the
+// target, or when every estimate dropped below restart_tol times its cycle's
+// starting residual (Table 1: mixed-precision restart criterion); every cycle
+// starts from the true FP64 residual b - D x.
 struct OuterResult {
   int iters = 0, restarts = 0;
-  double relres = 1;
+  std::vector<double> relres;
   bool converged = false;
 };
 
-OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu) {
+OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int R) {
   const FineGeom& g = c->g;
   const ddtm_params& p = c->p;
-  Blas B(c->stream, &c->scratch);
+  Blas B(c->stream, &c->scratch, &c->ring);
   int sp = p.smoother_prec, m = p.outer_restart;
-  size_t n = (size_t)g.V * 12;  // complex entries of a fine field
-  double* V = (double*)c->scratch.get("out_V", (m + 1) * n * 16);
-  char* Z = (char*)c->scratch.get("out_Z", (size_t)m * fine_field_bytes(g, sp));
-  float* Zn = (float*)c->scratch.get("out_Zn", (size_t)m * g.V * sizeof(float));
-  double* w = (double*)c->scratch.get("out_w", n * 16);
-  double* t64 = (double*)c->scratch.get("out_t64", n * 16);
-  void* vs = c->scratch.get("out_vs", fine_field_bytes(g, sp));
-  float* vsn = (float*)c->scratch.get("out_vsn", (size_t)g.V * sizeof(float));
-  auto Zj = [&](int j) { return (void*)(Z + (size_t)j * fine_field_bytes(g, sp)); };
-  auto Zjn = [&](int j) { return sp == PREC_F16 ? Zn + (size_t)j * g.V : (float*)nullptr; };
+  const size_t n = (size_t)g.V * 12;  // complex entries of one fine field
+  const size_t fb = fine_field_bytes(g, sp);
+  double* V = (double*)c->scratch.get("out_V", (size_t)(m + 1) * R * n * 16);
+  char* Z = (char*)c->scratch.get("out_Z", (size_t)m * R * fb);
+  float* Zn = (float*)c->scratch.get("out_Zn", (size_t)m * R * g.V * sizeof(float));
+  double* w = (double*)c->scratch.get("out_w", (size_t)R * n * 16);
+  double* t64 = (double*)c->scratch.get("out_t64", (size_t)R * n * 16);
+  char* vsb = (char*)c->scratch.get("out_vs", (size_t)R * fb);
+  float* vsn = (float*)c->scratch.get("out_vsn", (size_t)R * g.V * sizeof(float));
+  auto Zj = [&](int j, int r) { return (void*)(Z + ((size_t)j * R + r) * fb); };
+  auto Zjn = [&](int j, int r) { return sp == PREC_F16 ? Zn + ((size_t)j * R + r) * g.V : (float*)nullptr; };
+  auto Vj = [&](int j) { return V + 2 * (size_t)j * R * n; };
+  auto set = [&](const double* p0) { return VSet{(void*)p0, 0, n, R, false}; };
   auto D64 = [&](double* out, const double* in) {
-    launch_dslash(g, PREC_F64, out, nullptr, in, nullptr, c->links[0].p, c->clover[0].p, mu, c->stream);
+    for (int r = 0; r < R; r++)
+      launch_dslash(g, PREC_F64, out + 2 * (size_t)r * n, nullptr, in + 2 * (size_t)r * n, nullptr, c->links[0].p,
+                    c->clover[0].p, mu, c->stream);
   };
   OuterResult res;
-  double bn = sqrt(B.norm2(b, 0, n));
-  CK(cudaMemsetAsync(x, 0, n * 16, c->stream));
-  if (bn == 0) {
-    res.relres = 0;
-    res.converged = true;
-    return res;
-  }
-  std::vector<zc> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1);
-  std::vector<double2> h(m + 1), h2(m + 1);
+  res.relres.assign(R, 1.0);
+  std::vector<double> bn(R), beta(R), hn2(R), est(R);
+  B.norms2(set(b), bn.data());
+  for (int r = 0; r < R; r++) bn[r] = sqrt(bn[r]);
+  CK(cudaMemsetAsync(x, 0, (size_t)R * n * 16, c->stream));
+  std::vector<zc> H((size_t)R * (m + 1) * m), cs((size_t)R * m), sn((size_t)R * m), gv((size_t)R * (m + 1));
+  std::vector<double2> h((size_t)(m + 1) * R), h2((size_t)(m + 1) * R), coef(R), zero(R, make_double2(0, 0)),
+      one(R, make_double2(1, 0)), mone(R, make_double2(-1, 0));
+  auto Hat = [&](int r, int i, int j) -> zc& { return H[((size_t)r * (m + 1) + i) * m + j]; };
   bool first = true;
   while (true) {
-    // true residual r = b - D x into V_0
     if (first) {
-      CK(cudaMemcpyAsync(V, b, n * 16, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(Vj(0), b, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->stream));
     } else {
       D64(w, x);
-      CK(cudaMemcpyAsync(V, b, n * 16, cudaMemcpyDeviceToDevice, c->stream));
-      B.axpby(make_double2(-1, 0), w, 0, make_double2(1, 0), V, 0, n);
+      CK(cudaMemcpyAsync(Vj(0), b, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->stream));
+      B.axpby(mone.data(), set(w), one.data(), set(Vj(0)));
       res.restarts++;
     }
     first = false;
-    double beta = sqrt(B.norm2(V, 0, n));
-    res.relres = beta / bn;
-    if (!std::isfinite(res.relres)) throw Error(DDTM_ERR_NAN, "non-finite outer residual");
-    if (res.relres <= p.outer_tol) {
+    B.norms2(set(Vj(0)), beta.data());
+    bool done = true;
+    for (int r = 0; r < R; r++) {
+      beta[r] = sqrt(beta[r]);
+      res.relres[r] = bn[r] > 0 ? beta[r] / bn[r] : 0.0;
+      if (!std::isfinite(res.relres[r])) throw Error(DDTM_ERR_NAN, "non-finite outer residual");
+      done = done && res.relres[r] <= p.outer_tol;
+      coef[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
+    }
+    if (done) {
       res.converged = true;
       break;
     }
     if (res.iters >= p.outer_max_iters) break;
-    B.axpby(make_double2(0, 0), V, 0, make_double2(1.0 / beta, 0), V, 0, n);
+    B.axpby(zero.data(), set(Vj(0)), coef.data(), set(Vj(0)));
     std::fill(gv.begin(), gv.end(), zc(0));
-    gv[0] = beta;
+    for (int r = 0; r < R; r++) gv[(size_t)r * (m + 1)] = beta[r];
     int k = 0;
     for (int j = 0; j < m; j++) {
-      launch_field_convert(g, PREC_F64, V + 2 * (size_t)j * n, nullptr, sp, vs, vsn, c->stream);
-      mg_precondition(c, sp, Zj(j), Zjn(j), vs, vsn, mu);
-      launch_field_convert(g, sp, Zj(j), Zjn(j), PREC_F64, t64, nullptr, c->stream);
+      for (int r = 0; r < R; r++)
+        launch_field_convert(g, PREC_F64, Vj(j) + 2 * (size_t)r * n, nullptr, sp, vsb + (size_t)r * fb,
+                             sp == PREC_F16 ? vsn + (size_t)r * g.V : nullptr, c->stream);
+      mg_precondition(c, sp, Zj(j, 0), Zjn(j, 0), vsb, sp == PREC_F16 ? vsn : nullptr, mu, R);
+      for (int r = 0; r < R; r++)
+        launch_field_convert(g, sp, Zj(j, r), Zjn(j, r), PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
       D64(w, t64);
-      B.dots(V, 0, n, j + 1, w, 0, n, h.data());
-      B.multi_axpy(w, 0, V, 0, n, j + 1, h.data(), n, -1.0);
-      B.dots(V, 0, n, j + 1, w, 0, n, h2.data());
-      B.multi_axpy(w, 0, V, 0, n, j + 1, h2.data(), n, -1.0);
-      for (int i = 0; i <= j; i++) H[(size_t)i * m + j] = zc(h[i].x + h2[i].x, h[i].y + h2[i].y);
-      double hn = sqrt(B.norm2(w, 0, n));
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; i++) {
-        zc a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      B.dots(set(V), (size_t)R * n, j + 1, set(w), h.data());
+      B.maxpy(set(w), set(V), (size_t)R * n, j + 1, h.data(), -1.0, nullptr);
+      B.dots(set(V), (size_t)R * n, j + 1, set(w), h2.data());
+      B.maxpy(set(w), set(V), (size_t)R * n, j + 1, h2.data(), -1.0, hn2.data());
+      bool stop = true;
+      for (int r = 0; r < R; r++) {
+        double hn = sqrt(hn2[r]);
+        for (int i = 0; i <= j; i++)
+          Hat(r, i, j) = zc(h[(size_t)i * R + r].x + h2[(size_t)i * R + r].x, h[(size_t)i * R + r].y + h2[(size_t)i * R + r].y);
+        Hat(r, j + 1, j) = hn;
+        for (int i = 0; i < j; i++) {
+          zc a = Hat(r, i, j), bb = Hat(r, i + 1, j);
+          Hat(r, i, j) = std::conj(cs[(size_t)r * m + i]) * a + std::conj(sn[(size_t)r * m + i]) * bb;
+          Hat(r, i + 1, j) = -sn[(size_t)r * m + i] * a + cs[(size_t)r * m + i] * bb;
+        }
+        zc a = Hat(r, j, j);
+        double rho = sqrt(std::norm(a) + hn * hn);
+        cs[(size_t)r * m + j] = rho > 0 ? a / rho : zc(1);
+        sn[(size_t)r * m + j] = rho > 0 ? zc(hn / rho) : zc(0);
+        Hat(r, j, j) = rho;
+        Hat(r, j + 1, j) = 0;
+        zc* gr = &gv[(size_t)r * (m + 1)];
+        gr[j + 1] = -sn[(size_t)r * m + j] * gr[j];
+        gr[j] = std::conj(cs[(size_t)r * m + j]) * gr[j];
+        est[r] = std::abs(gr[j + 1]);
+        if (!std::isfinite(est[r])) throw Error(DDTM_ERR_NAN, "non-finite outer residual estimate");
+        bool ok = bn[r] == 0 || est[r] <= p.outer_tol * bn[r] || est[r] <= p.restart_tol * beta[r] || hn == 0;
+        stop = stop && ok;
+        coef[r] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0);
       }
-      zc a = H[(size_t)j * m + j];
-      double rho = sqrt(std::norm(a) + hn * hn);
-      cs[j] = rho > 0 ? a / rho : zc(1);
-      sn[j] = rho > 0 ? zc(hn / rho) : zc(0);
-      H[(size_t)j * m + j] = rho;
-      H[(size_t)(j + 1) * m + j] = 0;
-      gv[j + 1] = -sn[j] * gv[j];
-      gv[j] = std::conj(cs[j]) * gv[j];
       k = j + 1;
       res.iters++;
-      double est = std::abs(gv[j + 1]);
-      if (!std::isfinite(est)) throw Error(DDTM_ERR_NAN, "non-finite outer residual estimate");
-      if (est <= p.outer_tol * bn || est <= p.restart_tol * beta || hn == 0 || res.iters >= p.outer_max_iters) break;
-      B.axpby(make_double2(1.0 / hn, 0), w, 0, make_double2(0, 0), V + 2 * (size_t)(j + 1) * n, 0, n);  // V_{j+1} = w / hn
+      if (stop || res.iters >= p.outer_max_iters || j == m - 1) break;
+      B.axpby(coef.data(), set(w), zero.data(), set(Vj(j + 1)));  // V_{j+1} = w / hn
     }
-    std::vector<zc> y(k);
-    for (int i = k - 1; i >= 0; i--) {
-      zc s = gv[i];
-      for (int l = i + 1; l < k; l++) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
+    // x += sum_j y_j Z_j per system
+    std::vector<std::vector<zc>> ys(R, std::vector<zc>(k));
+    for (int r = 0; r < R; r++) {
+      for (int i = k - 1; i >= 0; i--) {
+        zc sacc = gv[(size_t)r * (m + 1) + i];
+        for (int l = i + 1; l < k; l++) sacc -= Hat(r, i, l) * ys[r][l];
+        zc d = Hat(r, i, i);
+        ys[r][i] = std::abs(d) > 0 ? sacc / d : zc(0);
+      }
     }
     for (int j = 0; j < k; j++) {
-      launch_field_convert(g, sp, Zj(j), Zjn(j), PREC_F64, t64, nullptr, c->stream);
-      B.axpby(make_double2(y[j].real(), y[j].imag()), t64, 0, make_double2(1, 0), x, 0, n);
+      for (int r = 0; r < R; r++) {
+        launch_field_convert(g, sp, Zj(j, r), Zjn(j, r), PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
+        coef[r] = make_double2(ys[r][j].real(), ys[r][j].imag());
+      }
+      B.axpby(coef.data(), set(t64), one.data(), set(x));
     }
   }
   return res;
@@ -361,13 +430,18 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu) {
 
 // ---- adaptive setup (Sec. 2.6) -----------------------------------------------------------------
 static void normalise_fields(ddtm_ctx* c, float2* tv, int nv) {
-  Blas B(c->stream, &c->scratch);
+  Blas B(c->stream, &c->scratch, &c->ring);
   size_t n = (size_t)c->g.V * 12;
+  VSet s{tv, 1, n, nv, false};
+  std::vector<double> nn(nv);
+  B.norms2(s, nn.data());
+  std::vector<double2> zero(nv, make_double2(0, 0)), sc(nv);
   for (int i = 0; i < nv; i++) {
-    double nn = sqrt(B.norm2(tv + (size_t)i * n, 1, n));
-    if (!(nn > 0) || !std::isfinite(nn)) throw Error(DDTM_ERR_NAN, "test vector vanished or became non-finite in setup");
-    B.axpby(make_double2(0, 0), tv + (size_t)i * n, 1, make_double2(1.0 / nn, 0), tv + (size_t)i * n, 1, n);
+    double q = sqrt(nn[i]);
+    if (!(q > 0) || !std::isfinite(q)) throw Error(DDTM_ERR_NAN, "test vector vanished or became non-finite in setup");
+    sc[i] = make_double2(1.0 / q, 0);
   }
+  B.axpby(zero.data(), s, sc.data(), s);
 }
 
 void run_setup(ddtm_ctx* c, double mu, uint64_t seed) {
@@ -380,25 +454,34 @@ void run_setup(ddtm_ctx* c, double mu, uint64_t seed) {
   float2* tv = c->tv0.as<float2>();
   for (int i = 0; i < nv; i++) launch_gaussian(tv + (size_t)i * n, n, seed * 0x100000001b3ull + (uint64_t)i * (n * 2 + 17), c->stream);
   int sp = p.smoother_prec;
-  void* bs = c->scratch.get("setup_b", fine_field_bytes(g, sp));
-  float* bsn = (float*)c->scratch.get("setup_bn", (size_t)g.V * 4);
-  void* xs = c->scratch.get("setup_x", fine_field_bytes(g, sp));
-  float* xsn = (float*)c->scratch.get("setup_xn", (size_t)g.V * 4);
-  // k = 1: SAP on each random vector
-  for (int i = 0; i < nv; i++) {
-    launch_field_convert(g, PREC_F32, tv + (size_t)i * n, nullptr, sp, bs, bsn, c->stream);
-    sap_run(c, sp, xs, xsn, bs, bsn, mu, p.post_smooth, p.nmr, true);
-    launch_field_convert(g, sp, xs, xsn, PREC_F32, tv + (size_t)i * n, nullptr, c->stream);
-  }
+  size_t fb = fine_field_bytes(g, sp);
+  char* bs = (char*)c->scratch.get("setup_b", (size_t)nv * fb);
+  float* bsn = (float*)c->scratch.get("setup_bn", (size_t)nv * g.V * 4);
+  char* xs = (char*)c->scratch.get("setup_x", (size_t)nv * fb);
+  float* xsn = (float*)c->scratch.get("setup_xn", (size_t)nv * g.V * 4);
+  auto to_sp = [&]() {
+    for (int i = 0; i < nv; i++)
+      launch_field_convert(g, PREC_F32, tv + (size_t)i * n, nullptr, sp, bs + (size_t)i * fb,
+                           sp == PREC_F16 ? bsn + (size_t)i * g.V : nullptr, c->stream);
+  };
+  auto from_sp = [&]() {
+    for (int i = 0; i < nv; i++)
+      launch_field_convert(g, sp, xs + (size_t)i * fb, sp == PREC_F16 ? xsn + (size_t)i * g.V : nullptr, PREC_F32,
+                           tv + (size_t)i * n, nullptr, c->stream);
+  };
+  float* bnp = sp == PREC_F16 ? bsn : nullptr;
+  float* xnp = sp == PREC_F16 ? xsn : nullptr;
+  // k = 1: the SAP smoother on every random vector, all vectors as one batch
+  to_sp();
+  sap_run(c, sp, xs, xnp, bs, bnp, mu, p.post_smooth, p.nmr, true, nv);
+  from_sp();
   normalise_fields(c, tv, nv);
   build_hierarchy(c);
-  // k >= 2: one multigrid iteration per test vector
+  // k >= 2: one multigrid iteration per test vector, all vectors as one batch
   for (int k = 2; k <= p.n_setup; k++) {
-    for (int i = 0; i < nv; i++) {
-      launch_field_convert(g, PREC_F32, tv + (size_t)i * n, nullptr, sp, bs, bsn, c->stream);
-      mg_precondition(c, sp, xs, xsn, bs, bsn, mu);
-      launch_field_convert(g, sp, xs, xsn, PREC_F32, tv + (size_t)i * n, nullptr, c->stream);
-    }
+    to_sp();
+    mg_precondition(c, sp, xs, xnp, bs, bnp, mu, nv);
+    from_sp();
     normalise_fields(c, tv, nv);
     build_hierarchy(c);
   }
@@ -450,7 +533,7 @@ int ddtm_sap(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int
     const double* din = stage_in(ctx, "canon_in", b + 2 * nsp * r, nsp, loc);
     double* dout = stage_out(ctx, "canon_out", x + 2 * nsp * r, nsp, loc);
     launch_spinor_from_canon(ctx->g, prec, fb.data.p, fb.nrm.as<float>(), din, ctx->stream);
-    sap_run(ctx, prec, fx.data.p, fx.nrm.as<float>(), fb.data.p, fb.nrm.as<float>(), mu, ncycles, nmr, true);
+    sap_run(ctx, prec, fx.data.p, fx.nrm.as<float>(), fb.data.p, fb.nrm.as<float>(), mu, ncycles, nmr, true, 1);
     launch_spinor_to_canon(ctx->g, prec, fx.data.p, fx.nrm.as<float>(), dout, ctx->stream);
     unstage_out(ctx, x + 2 * nsp * r, dout, nsp, loc);
   }
@@ -463,8 +546,8 @@ int ddtm_sap_field(ddtm_ctx* ctx, ddtm_field* x, const ddtm_field* b, double mu,
   if (!x || !b || x == b || x->ctx != ctx || b->ctx != ctx || x->prec != b->prec || x->nrhs != b->nrhs)
     throw Error(DDTM_ERR_ARG, "fields must differ and share context, precision and nrhs");
   if (ncycles < 0 || nmr < 0) throw Error(DDTM_ERR_ARG, "invalid cycle counts");
-  for (int r = 0; r < x->nrhs; r++)
-    sap_run(ctx, x->prec, field_ptr(x, r), field_nrm(x, r), field_ptr(b, r), field_nrm(b, r), mu, ncycles, nmr, true);
+  sap_run(ctx, x->prec, field_ptr(x, 0), field_nrm(x, 0), field_ptr(b, 0), field_nrm(b, 0), mu, ncycles, nmr, true,
+          x->nrhs);
   API_END(ctx)
 }
 
@@ -538,7 +621,7 @@ int ddtm_restrict(ddtm_ctx* ctx, int level, double* cout, const double* x, int n
     const double* din = stage_in(ctx, "canon_in", x + 2 * nsp * r, nsp, loc);
     double* dout = stage_out(ctx, "canon_cout", cout + 2 * nc * r, nc, loc);
     launch_spinor_from_canon(g, PREC_F32, f, nullptr, din, ctx->stream);
-    launch_restrict(g, PREC_F32, cv, f, nullptr, ctx->P0.p, PREC_F32, L.nv, ctx->stream);
+    launch_restrict(g, PREC_F32, cv, f, nullptr, ctx->P0.p, PREC_F32, L.nv, 1, 1, ctx->stream);
     B.axpby(make_double2(1, 0), cv, 1, make_double2(0, 0), dout, 0, nc);
     unstage_out(ctx, cout + 2 * nc * r, dout, nc, loc);
   }
@@ -561,7 +644,7 @@ int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* cin, int nrh
     const double* din = stage_in(ctx, "canon_cin", cin + 2 * nc * r, nc, loc);
     double* dout = stage_out(ctx, "canon_out", x + 2 * nsp * r, nsp, loc);
     B.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), cv, 1, nc);
-    launch_prolong(g, PREC_F32, f, nullptr, cv, ctx->P0.p, PREC_F32, L.nv, 0, ctx->stream);
+    launch_prolong(g, PREC_F32, f, nullptr, cv, ctx->P0.p, PREC_F32, L.nv, 1, 1, 0, ctx->stream);
     launch_spinor_to_canon(g, PREC_F32, f, nullptr, dout, ctx->stream);
     unstage_out(ctx, x + 2 * nsp * r, dout, nsp, loc);
   }
@@ -583,7 +666,7 @@ int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs
     const double* din = stage_in(ctx, "canon_cin", x + 2 * nc * r, nc, loc);
     double* dout = stage_out(ctx, "canon_cout", y + 2 * nc * r, nc, loc);
     B.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), xv, 1, nc);
-    launch_coarse_apply_full(L, yv, xv, mu, 3, 1.f, 0.f, ctx->stream);
+    launch_coarse_apply_full(L, yv, xv, 1, mu, 3, 1.f, 0.f, ctx->stream);
     B.axpby(make_double2(1, 0), yv, 1, make_double2(0, 0), dout, 0, nc);
     unstage_out(ctx, y + 2 * nc * r, dout, nc, loc);
   }
@@ -605,7 +688,7 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
   double* dout = stage_out(ctx, "canon_cout", x, nc, loc);
   B.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), bv, 1, nc);
   double rr;
-  int it = coarse_eo_solve(ctx, xv, bv, mu_c, ctx->p.coarse_restart, ctx->p.coarse_max_restarts, ctx->p.coarse_tol, &rr);
+  int it = coarse_eo_solve(ctx, xv, bv, 1, mu_c, ctx->p.coarse_restart, ctx->p.coarse_max_restarts, ctx->p.coarse_tol, &rr);
   B.axpby(make_double2(1, 0), xv, 1, make_double2(0, 0), dout, 0, nc);
   unstage_out(ctx, x, dout, nc, loc);
   CK(cudaStreamSynchronize(ctx->stream));
@@ -617,6 +700,21 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
   API_END(ctx)
 }
 
+// right-hand sides per outer batch: all of them if the FP64 basis, the stored
+// preconditioned vectors and the work fields fit in 60% of the free memory
+static int solve_batch(ddtm_ctx* ctx, int nrhs) {
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const FineGeom& g = ctx->g;
+  int m = ctx->p.outer_restart;
+  size_t per = (size_t)g.V * 12 * ((m + 1) * 16 + m * store2_bytes(ctx->p.smoother_prec) + 3 * 16 + 4 * 8) +
+               (size_t)g.V * (m + 2) * 4;
+  size_t budget = (size_t)(0.6 * (double)fr);
+  int R = per > 0 ? (int)(budget / per) : nrhs;
+  if (R < 1) R = 1;
+  return R < nrhs ? R : nrhs;
+}
+
 int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int loc, ddtm_solve_info* info) {
   API_BEGIN(ctx)
   check_loc(loc);
@@ -626,22 +724,28 @@ int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, i
   double t0 = now_s();
   const FineGeom& g = ctx->g;
   size_t nsp = (size_t)g.V * 12;
-  double* bf = (double*)ctx->scratch.get("solve_b", nsp * 16);
-  double* xf = (double*)ctx->scratch.get("solve_x", nsp * 16);
   ddtm_solve_info acc;
   memset(&acc, 0, sizeof(acc));
   ctx->coarse_iters = 0;
   bool all_conv = true;
-  for (int r = 0; r < nrhs; r++) {
-    const double* din = stage_in(ctx, "canon_in", b + 2 * nsp * r, nsp, loc);
-    double* dout = stage_out(ctx, "canon_out", x + 2 * nsp * r, nsp, loc);
-    launch_spinor_from_canon(g, PREC_F64, bf, nullptr, din, ctx->stream);
-    OuterResult o = outer_fgmres(ctx, xf, bf, mu);
-    launch_spinor_to_canon(g, PREC_F64, xf, nullptr, dout, ctx->stream);
-    unstage_out(ctx, x + 2 * nsp * r, dout, nsp, loc);
+  int batch = nrhs > 0 ? solve_batch(ctx, nrhs) : 1;
+  for (int r0 = 0; r0 < nrhs; r0 += batch) {
+    int R = nrhs - r0 < batch ? nrhs - r0 : batch;
+    double* bf = (double*)ctx->scratch.get("solve_b", (size_t)R * nsp * 16);
+    double* xf = (double*)ctx->scratch.get("solve_x", (size_t)R * nsp * 16);
+    for (int r = 0; r < R; r++) {
+      const double* din = stage_in(ctx, "canon_in", b + 2 * nsp * (r0 + r), nsp, loc);
+      launch_spinor_from_canon(g, PREC_F64, bf + 2 * nsp * r, nullptr, din, ctx->stream);
+    }
+    OuterResult o = outer_fgmres(ctx, xf, bf, mu, R);
+    for (int r = 0; r < R; r++) {
+      double* dout = stage_out(ctx, "canon_out", x + 2 * nsp * (r0 + r), nsp, loc);
+      launch_spinor_to_canon(g, PREC_F64, xf + 2 * nsp * r, nullptr, dout, ctx->stream);
+      unstage_out(ctx, x + 2 * nsp * (r0 + r), dout, nsp, loc);
+    }
     acc.iters = o.iters > acc.iters ? o.iters : acc.iters;
     acc.restarts = o.restarts > acc.restarts ? o.restarts : acc.restarts;
-    acc.max_relres = o.relres > acc.max_relres ? o.relres : acc.max_relres;
+    for (double v : o.relres) acc.max_relres = v > acc.max_relres ? v : acc.max_relres;
     all_conv = all_conv && o.converged;
   }
   CK(cudaStreamSynchronize(ctx->stream));

@@ -20,10 +20,10 @@ void* field_ptr(const ddtm_field* f, int r);
 float* field_nrm(const ddtm_field* f, int r);
 void dslash_field(ddtm_ctx* c, ddtm_field* y, const ddtm_field* x, double mu);
 
-// ncycles red-black SAP cycles on D(mu) x = b from x = 0 (fields of one rhs,
-// precision prec); x and b are internal-layout device pointers.
+// ncycles red-black SAP cycles on D(mu) x = b (from x = 0 if from_zero) for R
+// right-hand sides: fields of precision prec at stride 12 V, FP16 scales at stride V.
 void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const float* bn, double mu, int ncycles,
-             int nmr, bool from_zero);
+             int nmr, bool from_zero, int R);
 
 void validate_params(ddtm_ctx* c, const ddtm_params& p);
 void invalidate_setup(ddtm_ctx* c);

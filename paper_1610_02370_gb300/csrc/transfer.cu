@@ -94,110 +94,166 @@ __device__ __forceinline__ cplx<float> ldp<float2>(const float2* p) { return ld(
 template <>
 __device__ __forceinline__ cplx<float> ldp<__half2>(const __half2* p) { return ld(p); }
 
-// c = P^dagger psi per aggregate.  One CTA per block: psi_B staged in shared
-// memory (FP32, [12][Vb]); warp w computes outputs o = w, w + nwarps, ...,
-// lanes striding over sites, then a warp reduction.
-template <int PI, typename PS>
-__global__ void k_restrict(cplx<float>* __restrict__ c, Spinor<PI> psi, const PS* __restrict__ P, int nv) {
+// c = P^dagger psi per aggregate for a batch of R fine fields (field r at
+// psi + r * fstride, its FP16 scales at pn + r * V); c interleaved,
+// c[(blk * n + o) * R + r].  One CTA per block and chunk of RC right-hand
+// sides: the RC block vectors are staged in shared memory (FP32, [rc][12][Vb]);
+// warp w computes outputs o = w, w + nwarps, ... for all RC of them, lanes
+// striding over sites, then warp reductions.
+template <int PI, typename PS, int RC>
+__global__ void k_restrict(cplx<float>* __restrict__ c, Spinor<PI> psi, size_t fstride, long V, const PS* __restrict__ P,
+                           int nv, int R, int Rs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<float>* sp = reinterpret_cast<cplx<float>*>(smem_raw);
   const int Vb = psi.Vb;
   const int blk = blockIdx.x;
-  for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
-    cplx<typename Prec<PI>::real> v[12];
-    psi.load(blk, loc, v);
+  const int r0 = blockIdx.y * RC;
+  const int nr = R - r0 < RC ? R - r0 : RC;
+  for (int rc = 0; rc < nr; rc++) {
+    Spinor<PI> f = psi;
+    f.d += (size_t)(r0 + rc) * fstride;
+    if (f.nrm) f.nrm += (size_t)(r0 + rc) * V;
+    for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
+      cplx<typename Prec<PI>::real> v[12];
+      f.load(blk, loc, v);
 #pragma unroll
-    for (int k = 0; k < 12; k++) sp[k * Vb + loc] = cplx<float>((float)v[k].re, (float)v[k].im);
+      for (int k = 0; k < 12; k++) sp[((size_t)rc * 12 + k) * Vb + loc] = cplx<float>((float)v[k].re, (float)v[k].im);
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = 2 * nv;
   for (int o = w; o < n; o += nw) {
     int s = o / nv, i = o - s * nv;
-    cplx<float> acc(0, 0);
+    cplx<float> acc[RC];
+#pragma unroll
+    for (int rc = 0; rc < RC; rc++) acc[rc] = cplx<float>(0, 0);
     const PS* col = P + ((size_t)(blk * 2 + s) * nv + i) * 6 * Vb;
     for (int comp = 0; comp < 6; comp++)
-      for (int loc = lane; loc < Vb; loc += 32) cmac_conj(acc, ldp<PS>(col + comp * Vb + loc), sp[(6 * s + comp) * Vb + loc]);
-    acc.re = warp_sum(acc.re);
-    acc.im = warp_sum(acc.im);
-    if (lane == 0) c[(size_t)blk * n + o] = acc;
+      for (int loc = lane; loc < Vb; loc += 32) {
+        cplx<float> pv = ldp<PS>(col + comp * Vb + loc);
+#pragma unroll
+        for (int rc = 0; rc < RC; rc++)
+          if (rc < nr) cmac_conj(acc[rc], pv, sp[((size_t)rc * 12 + 6 * s + comp) * Vb + loc]);
+      }
+#pragma unroll
+    for (int rc = 0; rc < RC; rc++) {
+      acc[rc].re = warp_sum(acc[rc].re);
+      acc[rc].im = warp_sum(acc[rc].im);
+      if (lane == 0 && rc < nr) c[((size_t)blk * n + o) * Rs + r0 + rc] = acc[rc];
+    }
   }
 }
 
-// x = P e (mode 0) or x += P e (mode 1).  One CTA per block, thread = site;
-// e_B staged in shared memory.
-template <int PO, typename PS>
-__global__ void k_prolong(Spinor<PO> x, const cplx<float>* __restrict__ e, const PS* __restrict__ P, int nv, int add) {
+// x_r = P e_r (add = 0) or x_r += P e_r (add = 1) for a batch of R fields; e
+// interleaved.  One CTA per block, thread = site; e_B (n x R) staged in shared
+// memory; each P entry loaded once per thread serves RC right-hand sides.
+template <int PO, typename PS, int RC>
+__global__ void k_prolong(Spinor<PO> x, size_t fstride, long V, const cplx<float>* __restrict__ e, const PS* __restrict__ P,
+                          int nv, int R, int Rs, int add) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<float>* se = reinterpret_cast<cplx<float>*>(smem_raw);
+  typedef typename Prec<PO>::real Rl;
   const int Vb = x.Vb;
   const int blk = blockIdx.x;
   const int n = 2 * nv;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) se[k] = e[(size_t)blk * n + k];
+  for (int k = threadIdx.x; k < n * Rs; k += blockDim.x) se[k] = e[(size_t)blk * n * Rs + k];
   __syncthreads();
   for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
-    typedef typename Prec<PO>::real R;
-    cplx<R> out[12];
-    if (add) x.loadw(blk, loc, out);
-    for (int s = 0; s < 2; s++)
-      for (int comp = 0; comp < 6; comp++) {
-        cplx<float> acc(0, 0);
-        for (int i = 0; i < nv; i++)
-          cmac(acc, ldp<PS>(P + (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc), se[s * nv + i]);
-        cplx<R> a((R)acc.re, (R)acc.im);
-        out[6 * s + comp] = add ? out[6 * s + comp] + a : a;
+    for (int r0 = 0; r0 < R; r0 += RC) {
+      const int nr = R - r0 < RC ? R - r0 : RC;
+      cplx<float> acc[RC][12];
+#pragma unroll
+      for (int rc = 0; rc < RC; rc++)
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[rc][k] = cplx<float>(0, 0);
+      for (int s = 0; s < 2; s++)
+        for (int i = 0; i < nv; i++) {
+          cplx<float> ev[RC];
+#pragma unroll
+          for (int rc = 0; rc < RC; rc++) ev[rc] = rc < nr ? se[(s * nv + i) * Rs + r0 + rc] : cplx<float>(0, 0);
+          const PS* col = P + ((size_t)(blk * 2 + s) * nv + i) * 6 * Vb + loc;
+#pragma unroll
+          for (int comp = 0; comp < 6; comp++) {
+            cplx<float> pv = ldp<PS>(col + (size_t)comp * Vb);
+#pragma unroll
+            for (int rc = 0; rc < RC; rc++) cmac(acc[rc][6 * s + comp], pv, ev[rc]);
+          }
+        }
+#pragma unroll
+      for (int rc = 0; rc < RC; rc++) {
+        if (rc >= nr) break;
+        Spinor<PO> f = x;
+        f.d += (size_t)(r0 + rc) * fstride;
+        if (f.nrm) f.nrm += (size_t)(r0 + rc) * V;
+        cplx<Rl> out[12];
+        if (add) f.loadw(blk, loc, out);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+          cplx<Rl> a((Rl)acc[rc][k].re, (Rl)acc[rc][k].im);
+          out[k] = add ? out[k] + a : a;
+        }
+        f.store(blk, loc, out);
       }
-    x.store(blk, loc, out);
+    }
   }
 }
 
-template <typename PS>
-static void restrict_t(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const PS* P, int nv,
-                       cudaStream_t st) {
-  size_t smem = (size_t)12 * g.Vb * sizeof(cplx<float>);
-  int threads = 256;
-  if (pin == PREC_F64) {
-    static bool cfg = false;
-    if (!cfg) { CK(cudaFuncSetAttribute(k_restrict<PREC_F64, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000)); cfg = true; }
-    k_restrict<PREC_F64, PS><<<g.Nb, threads, smem, st>>>(c, Spinor<PREC_F64>{(double2*)psi, nullptr, g.Vb}, P, nv);
-  } else if (pin == PREC_F32) {
-    static bool cfg = false;
-    if (!cfg) { CK(cudaFuncSetAttribute(k_restrict<PREC_F32, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000)); cfg = true; }
-    k_restrict<PREC_F32, PS><<<g.Nb, threads, smem, st>>>(c, Spinor<PREC_F32>{(float2*)psi, nullptr, g.Vb}, P, nv);
-  } else {
-    static bool cfg = false;
-    if (!cfg) { CK(cudaFuncSetAttribute(k_restrict<PREC_F16, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000)); cfg = true; }
-    k_restrict<PREC_F16, PS><<<g.Nb, threads, smem, st>>>(c, Spinor<PREC_F16>{(__half2*)psi, (float*)pn, g.Vb}, P, nv);
+static const int RST_RC = 4, PRO_RC = 2;
+
+template <int PI, typename PS>
+static void restrict_p(const FineGeom& g, cplx<float>* c, Spinor<PI> f, size_t fstride, const PS* P, int nv, int R,
+                       int Rs, cudaStream_t st) {
+  size_t smem = (size_t)RST_RC * 12 * g.Vb * sizeof(cplx<float>);
+  static bool cfg = false;
+  if (!cfg) {
+    CK(cudaFuncSetAttribute(k_restrict<PI, PS, RST_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    cfg = true;
   }
+  dim3 grid(g.Nb, (R + RST_RC - 1) / RST_RC);
+  k_restrict<PI, PS, RST_RC><<<grid, 256, smem, st>>>(c, f, fstride, g.V, P, nv, R, Rs);
+}
+
+template <typename PS>
+static void restrict_t(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const PS* P, int nv, int R,
+                       int Rs, cudaStream_t st) {
+  size_t fs = (size_t)g.V * 12;
+  if (pin == PREC_F64) restrict_p<PREC_F64, PS>(g, c, Spinor<PREC_F64>{(double2*)psi, nullptr, g.Vb}, fs, P, nv, R, Rs, st);
+  else if (pin == PREC_F32) restrict_p<PREC_F32, PS>(g, c, Spinor<PREC_F32>{(float2*)psi, nullptr, g.Vb}, fs, P, nv, R, Rs, st);
+  else restrict_p<PREC_F16, PS>(g, c, Spinor<PREC_F16>{(__half2*)psi, (float*)pn, g.Vb}, fs, P, nv, R, Rs, st);
   CKL("restrict");
 }
 
 template <typename PS>
-static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const PS* P, int nv, int add,
-                      cudaStream_t st) {
-  size_t smem = (size_t)2 * nv * sizeof(cplx<float>);
+static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const PS* P, int nv, int R,
+                      int Rs, int add, cudaStream_t st) {
+  size_t smem = (size_t)2 * nv * Rs * sizeof(cplx<float>);
   int threads = g.Vb < 128 ? ((g.Vb + 31) / 32) * 32 : 128;
+  size_t fs = (size_t)g.V * 12;
   if (pout == PREC_F64)
-    k_prolong<PREC_F64, PS><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F64>{(double2*)x, nullptr, g.Vb}, e, P, nv, add);
+    k_prolong<PREC_F64, PS, PRO_RC><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F64>{(double2*)x, nullptr, g.Vb}, fs, g.V, e,
+                                                                 P, nv, R, Rs, add);
   else if (pout == PREC_F32)
-    k_prolong<PREC_F32, PS><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F32>{(float2*)x, nullptr, g.Vb}, e, P, nv, add);
+    k_prolong<PREC_F32, PS, PRO_RC><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F32>{(float2*)x, nullptr, g.Vb}, fs, g.V, e,
+                                                                 P, nv, R, Rs, add);
   else
-    k_prolong<PREC_F16, PS><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F16>{(__half2*)x, xn, g.Vb}, e, P, nv, add);
+    k_prolong<PREC_F16, PS, PRO_RC><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F16>{(__half2*)x, xn, g.Vb}, fs, g.V, e, P,
+                                                                 nv, R, Rs, add);
   CKL("prolong");
 }
 
 void launch_restrict(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const void* P,
-                     int pprec, int nv, cudaStream_t st) {
+                     int pprec, int nv, int R, int Rs, cudaStream_t st) {
   ScopedTimer timer_(pin == PREC_F16 ? "restrict_f16" : pin == PREC_F32 ? "restrict_f32" : "restrict_f64", st);
-  if (pprec == PREC_F16) restrict_t<__half2>(g, pin, c, psi, pn, (const __half2*)P, nv, st);
-  else restrict_t<float2>(g, pin, c, psi, pn, (const float2*)P, nv, st);
+  if (pprec == PREC_F16) restrict_t<__half2>(g, pin, c, psi, pn, (const __half2*)P, nv, R, Rs, st);
+  else restrict_t<float2>(g, pin, c, psi, pn, (const float2*)P, nv, R, Rs, st);
 }
 
 void launch_prolong(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const void* P, int pprec,
-                    int nv, int add, cudaStream_t st) {
+                    int nv, int R, int Rs, int add, cudaStream_t st) {
   ScopedTimer timer_(pout == PREC_F16 ? "prolong_f16" : pout == PREC_F32 ? "prolong_f32" : "prolong_f64", st);
-  if (pprec == PREC_F16) prolong_t<__half2>(g, pout, x, xn, e, (const __half2*)P, nv, add, st);
-  else prolong_t<float2>(g, pout, x, xn, e, (const float2*)P, nv, add, st);
+  if (pprec == PREC_F16) prolong_t<__half2>(g, pout, x, xn, e, (const __half2*)P, nv, R, Rs, add, st);
+  else prolong_t<float2>(g, pout, x, xn, e, (const float2*)P, nv, R, Rs, add, st);
 }
 
 __global__ void k_P_to_half(const float2* __restrict__ P, __half2* __restrict__ Ph, size_t n) {
