@@ -77,13 +77,13 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc):
         fine = V * (12 * s2 + nrm)
         return V * 12 * nv * pbytes + fine * (2 if name.startswith("prolong") else 1) + Nc * n * 8
     if name.startswith("coarse_even_"):
+        # 8 hop blocks and the FP32 self-block inverse per even site, read once per batch of NRHS
         d = S2[prec]
-        ne = Nc / 2
-        return ne * (8 * n * n * d + n * n * 8 + 8 * n * 8 + 2 * n * 8)
+        return Nc / 2 * (8 * n * n * d + n * n * 8 + 2 * n * NRHS * 8)
     if name.startswith("coarse_apply_odd_"):
+        # launches alternate the self block (1 block) and the 8 hop blocks: 4.5 blocks per odd site on average
         d = S2[prec]
-        no = Nc / 2
-        return no * (4.5 * n * n * d + 5 * n * 8)  # launches alternate self (1 block) and hop (8 blocks)
+        return Nc / 2 * (4.5 * n * n * d + 3 * n * NRHS * 8)
     return None
 
 

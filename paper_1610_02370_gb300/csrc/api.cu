@@ -109,6 +109,36 @@ void dslash_field(ddtm_ctx* c, ddtm_field* y, const ddtm_field* x, double mu) {
 
 }  // namespace ddtm
 
+void* ddtm_ctx::scratch_host(const std::string& name, size_t bytes) {
+  auto it = host_bufs.find(name);
+  if (it != host_bufs.end() && it->second.second >= bytes) return it->second.first;
+  if (it != host_bufs.end()) cudaFreeHost(it->second.first);
+  void* p = nullptr;
+  CK(cudaMallocHost(&p, bytes));
+  host_bufs[name] = std::make_pair(p, bytes);
+  return p;
+}
+
+void ddtm_ctx::events(const std::string& name, cudaEvent_t ev[2]) {
+  auto it = event_pairs.find(name);
+  if (it == event_pairs.end()) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    it = event_pairs.emplace(name, std::make_pair(a, b)).first;
+  }
+  ev[0] = it->second.first;
+  ev[1] = it->second.second;
+}
+
+ddtm_ctx::~ddtm_ctx() {
+  for (auto& kv : host_bufs) cudaFreeHost(kv.second.first);
+  for (auto& kv : event_pairs) {
+    cudaEventDestroy(kv.second.first);
+    cudaEventDestroy(kv.second.second);
+  }
+}
+
 extern "C" {
 
 int ddtm_default_params(ddtm_params* p) {

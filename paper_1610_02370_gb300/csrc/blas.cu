@@ -19,6 +19,14 @@ template <typename T> __device__ __forceinline__ void st2(T* p, size_t i, double
 template <> __device__ __forceinline__ void st2<float2>(float2* p, size_t i, double re, double im) { p[i] = make_float2((float)re, (float)im); }
 template <> __device__ __forceinline__ void st2<double2>(double2* p, size_t i, double re, double im) { p[i] = make_double2(re, im); }
 
+// Arithmetic precision of an operation on two vector types: FP32 when both
+// are FP32 (per-thread partial sums are then short, and every cross-thread
+// reduction is FP64), FP64 otherwise.
+template <typename A, typename B> struct Acc { typedef double T; };
+template <> struct Acc<float2, float2> { typedef float T; };
+template <typename T> __device__ __forceinline__ cplx<T> ldc(const float2* p, size_t i) { float2 a = p[i]; return cplx<T>((T)a.x, (T)a.y); }
+template <typename T> __device__ __forceinline__ cplx<T> ldc(const double2* p, size_t i) { double2 a = p[i]; return cplx<T>((T)a.x, (T)a.y); }
+
 // Per-rhs reduction inside a CTA for interleaved sets: thread t holds the
 // partial of right-hand side t % R (blockDim is a multiple of R); thread r < R
 // returns the sum over threads r, r + R, ... in that order.
@@ -58,25 +66,29 @@ __global__ void k_bdots(const TV* __restrict__ V, size_t ldv, int nvec, const TW
     const size_t chunk = ((N + (size_t)G * bd - 1) / ((size_t)G * bd)) * bd;
     const size_t beg = (size_t)blockIdx.x * chunk, end = beg + chunk < N ? beg + chunk : N;
     const TV* vj = V + (size_t)j * ldv;
-    double2 acc = make_double2(0, 0);
+    typedef typename Acc<TV, TW>::T AT;
+    AT are = 0, aim = 0;
     for (size_t i = beg + threadIdx.x; i < end; i += bd) {
-      double2 x = ld2(vj, i), y = ld2(w, i);
-      acc.x += x.x * y.x + x.y * y.y;
-      acc.y += x.x * y.y - x.y * y.x;
+      auto x = ldc<AT>(vj, i);
+      auto y = ldc<AT>(w, i);
+      are += x.re * y.re + x.im * y.im;
+      aim += x.re * y.im - x.im * y.re;
     }
-    double2 s = rhs_reduce(acc, R, red);
+    double2 s = rhs_reduce(make_double2(are, aim), R, red);
     if ((int)threadIdx.x < R) partial[((size_t)j * R + threadIdx.x) * G + blockIdx.x] = s;
   } else {
     const int jr = blockIdx.y, j = jr / R, r = jr - j * R;
     const TV* a = V + (size_t)j * ldv + (size_t)r * n;
     const TW* b = w + (size_t)r * n;
-    double2 acc = make_double2(0, 0);
+    typedef typename Acc<TV, TW>::T AT;
+    AT are = 0, aim = 0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)G * blockDim.x) {
-      double2 x = ld2(a, i), y = ld2(b, i);
-      acc.x += x.x * y.x + x.y * y.y;
-      acc.y += x.x * y.y - x.y * y.x;
+      auto x = ldc<AT>(a, i);
+      auto y = ldc<AT>(b, i);
+      are += x.re * y.re + x.im * y.im;
+      aim += x.re * y.im - x.im * y.re;
     }
-    double2 s = cta_reduce(acc, reinterpret_cast<double*>(red));
+    double2 s = cta_reduce(make_double2(are, aim), reinterpret_cast<double*>(red));
     if (threadIdx.x == 0) partial[(size_t)jr * G + blockIdx.x] = s;
   }
 }
@@ -112,15 +124,17 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
     const size_t N = n * R, stride = (size_t)G * blockDim.x;  // stride is a multiple of R
     const int r = threadIdx.x % R;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-      double2 acc = ld2(w, i);
+      typedef typename Acc<TV, TW>::T AT;
+      auto acc = ldc<AT>(w, i);
       for (int j = 0; j < nvec; j++) {
-        double2 v = ld2(V + (size_t)j * ldv, i), c = sc[j * R + r];
-        acc.x += sign * (c.x * v.x - c.y * v.y);
-        acc.y += sign * (c.x * v.y + c.y * v.x);
+        auto v = ldc<AT>(V + (size_t)j * ldv, i);
+        double2 c = sc[j * R + r];
+        AT cr = (AT)(sign * c.x), ci = (AT)(sign * c.y);
+        acc.re += cr * v.re - ci * v.im;
+        acc.im += cr * v.im + ci * v.re;
       }
-      st2(w, i, acc.x, acc.y);
-      double2 back = ld2(w, i);  // norm of the stored (rounded) vector
-      nn += back.x * back.x + back.y * back.y;
+      st2(w, i, acc.re, acc.im);
+      nn += (double)(acc.re * acc.re + acc.im * acc.im);
     }
     if (npartial) {
       double2 s = rhs_reduce(make_double2(nn, 0), R, red);
@@ -130,15 +144,17 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
     TW* wr = w + (size_t)r_sep * n;
     const TV* Vr = V + (size_t)r_sep * n;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)G * blockDim.x) {
-      double2 acc = ld2(wr, i);
+      typedef typename Acc<TV, TW>::T AT;
+      auto acc = ldc<AT>(wr, i);
       for (int j = 0; j < nvec; j++) {
-        double2 v = ld2(Vr + (size_t)j * ldv, i), c = sc[j];
-        acc.x += sign * (c.x * v.x - c.y * v.y);
-        acc.y += sign * (c.x * v.y + c.y * v.x);
+        auto v = ldc<AT>(Vr + (size_t)j * ldv, i);
+        double2 c = sc[j];
+        AT cr = (AT)(sign * c.x), ci = (AT)(sign * c.y);
+        acc.re += cr * v.re - ci * v.im;
+        acc.im += cr * v.im + ci * v.re;
       }
-      st2(wr, i, acc.x, acc.y);
-      double2 back = ld2(wr, i);
-      nn += back.x * back.x + back.y * back.y;
+      st2(wr, i, acc.re, acc.im);
+      nn += (double)(acc.re * acc.re + acc.im * acc.im);
     }
     if (npartial) {
       double2 s = cta_reduce(make_double2(nn, 0), reinterpret_cast<double*>(red));
@@ -159,6 +175,17 @@ __global__ void k_baxpby(const double2* __restrict__ a, const TX* x, const doubl
     double re = ca.x * u.x - ca.y * u.y + cb.x * v.x - cb.y * v.y;
     double im = ca.x * u.y + ca.y * u.x + cb.x * v.y + cb.y * v.x;
     st2(y, i, re, im);
+  }
+}
+
+// y(., r) = a[r] x(., r)  (x may equal y)
+template <typename TX, typename TY, bool INTER>
+__global__ void k_bscale(const double2* __restrict__ a, const TX* x, TY* y, size_t n, int R) {
+  const size_t N = n * R;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = INTER ? (int)(i % R) : (int)(i / n);
+    const double2 ca = a[r], u = ld2(x, i);
+    st2(y, i, ca.x * u.x - ca.y * u.y, ca.x * u.y + ca.y * u.x);
   }
 }
 
@@ -322,6 +349,62 @@ void Blas::axpby(const double2* a_host, const VSet& x, const double2* b_host, co
   CKL("baxpby");
 }
 
+void Blas::dots_dev(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_dev) {
+  ScopedTimer timer_("blas_dots", st);
+  const int R = w.R;
+  if (nvec <= 0) return;
+  int bd = w.inter ? inter_block(R) : 256;
+  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  double2* partial = (double2*)pool->get("blas_partial_dev", (size_t)nvec * R * G * sizeof(double2));
+  dim3 grid(G, w.inter ? nvec : nvec * R);
+  if (grid.y > 65535) throw Error(DDTM_ERR_ARG, "internal: too many vectors in one inner-product batch");
+  if (w.inter)
+    DISPATCH_TYPES(V.type, w.type,
+                   (k_bdots<A, B, true><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
+  else
+    DISPATCH_TYPES(V.type, w.type,
+                   (k_bdots<A, B, false><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
+  CKL("bdots");
+  k_reduce_partials<<<nvec * R, 128, 0, st>>>(partial, G, out_dev);
+  CKL("reduce_partials");
+}
+
+void Blas::maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev, double sign,
+                     double2* norms2_dev) {
+  ScopedTimer timer_("blas_maxpy", st);
+  const int R = w.R;
+  int bd = w.inter ? inter_block(R) : 256;
+  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  double2* npart = norms2_dev ? (double2*)pool->get("blas_npartial_dev", (size_t)R * G * sizeof(double2)) : nullptr;
+  size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
+  if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");
+  dim3 grid(G, w.inter ? 1 : R);
+  if (w.inter)
+    DISPATCH_TYPES(V.type, w.type,
+                   (maxpy_launch<A, B, true>(grid, bd, smem, st, (B*)w.p, (const A*)V.p, ldv, nvec, coef_dev, w.n, R, sign, npart)));
+  else
+    DISPATCH_TYPES(V.type, w.type,
+                   (maxpy_launch<A, B, false>(grid, bd, smem, st, (B*)w.p, (const A*)V.p, ldv, nvec, coef_dev, w.n, R, sign, npart)));
+  CKL("bmaxpy");
+  if (norms2_dev) {
+    k_reduce_partials<<<R, 128, 0, st>>>(npart, G, norms2_dev);
+    CKL("reduce_partials");
+  }
+}
+
+void Blas::scale_dev(const double2* a_dev, const VSet& x, const VSet& y) {
+  ScopedTimer timer_("blas_axpby", st);
+  const int R = y.R;
+  size_t N = y.n * R;
+  size_t gsz = (N + 255) / 256;
+  unsigned grid = (unsigned)(gsz < 1 ? 1 : (gsz > 8192 ? 8192 : gsz));
+  if (y.inter)
+    DISPATCH_TYPES(x.type, y.type, (k_bscale<A, B, true><<<grid, 256, 0, st>>>(a_dev, (const A*)x.p, (B*)y.p, y.n, R)));
+  else
+    DISPATCH_TYPES(x.type, y.type, (k_bscale<A, B, false><<<grid, 256, 0, st>>>(a_dev, (const A*)x.p, (B*)y.p, y.n, R)));
+  CKL("bscale");
+}
+
 double Blas::norm2(const void* a, int t, size_t n) {
   double r;
   norms2(VSet{(void*)a, t, n, 1, true}, &r);
@@ -330,6 +413,87 @@ double Blas::norm2(const void* a, int t, size_t n) {
 
 void Blas::axpby(double2 a, const void* x, int tx, double2 b, void* y, int ty, size_t n) {
   axpby(&a, VSet{(void*)x, tx, n, 1, true}, &b, VSet{y, ty, n, 1, true});
+}
+
+// ---- Arnoldi bookkeeping kernels (one thread per system) ------------------------------
+__device__ __forceinline__ cplx<double> zc2(double2 v) { return cplx<double>(v.x, v.y); }
+__device__ __forceinline__ double2 zd2(cplx<double> v) { return make_double2(v.re, v.im); }
+
+__global__ void k_arnoldi_start(ArnoldiDev a, const double2* __restrict__ nr2) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.R) return;
+  double beta = sqrt(nr2[r].x);
+  for (int i = 0; i <= a.m; i++) a.g[(size_t)r * (a.m + 1) + i] = make_double2(0, 0);
+  a.g[(size_t)r * (a.m + 1)] = make_double2(beta, 0);
+  a.est[r] = a.bn[r] > 0 ? beta / a.bn[r] : 0.0;
+  a.scale[r] = make_double2(beta > 0 ? 1.0 / beta : 0.0, 0);
+}
+
+__global__ void k_arnoldi_step(ArnoldiDev a, int j, const double2* __restrict__ h, const double2* __restrict__ h2,
+                               const double2* __restrict__ hn2) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.R) return;
+  const int m = a.m, R = a.R;
+  double2* H = a.H + (size_t)r * (m + 1) * m;
+  for (int i = 0; i <= j; i++) {
+    double2 v = h[(size_t)i * R + r];
+    if (h2) { v.x += h2[(size_t)i * R + r].x; v.y += h2[(size_t)i * R + r].y; }
+    H[(size_t)i * m + j] = v;
+  }
+  double hn = sqrt(hn2[r].x);
+  H[(size_t)(j + 1) * m + j] = make_double2(hn, 0);
+  for (int i = 0; i < j; i++) {
+    cplx<double> x = zc2(H[(size_t)i * m + j]), y = zc2(H[(size_t)(i + 1) * m + j]);
+    cplx<double> c = zc2(a.cs[(size_t)r * m + i]), s = zc2(a.sn[(size_t)r * m + i]);
+    H[(size_t)i * m + j] = zd2(conj(c) * x + conj(s) * y);
+    H[(size_t)(i + 1) * m + j] = zd2(c * y - s * x);
+  }
+  cplx<double> d = zc2(H[(size_t)j * m + j]);
+  double rho = sqrt(norm2(d) + hn * hn);
+  cplx<double> c = rho > 0 ? cplx<double>(d.re / rho, d.im / rho) : cplx<double>(1, 0);
+  cplx<double> s = rho > 0 ? cplx<double>(hn / rho, 0) : cplx<double>(0, 0);
+  a.cs[(size_t)r * m + j] = zd2(c);
+  a.sn[(size_t)r * m + j] = zd2(s);
+  H[(size_t)j * m + j] = make_double2(rho, 0);
+  H[(size_t)(j + 1) * m + j] = make_double2(0, 0);
+  double2* g = a.g + (size_t)r * (m + 1);
+  cplx<double> gj = zc2(g[j]);
+  g[j + 1] = zd2(-(s * gj));
+  g[j] = zd2(conj(c) * gj);
+  double e = sqrt(norm2(zc2(g[j + 1])));
+  a.est[r] = a.bn[r] > 0 ? e / a.bn[r] : 0.0;
+  a.scale[r] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0);
+}
+
+__global__ void k_arnoldi_solve(ArnoldiDev a, int k, double2* __restrict__ y) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.R) return;
+  const int m = a.m, R = a.R;
+  const double2* H = a.H + (size_t)r * (m + 1) * m;
+  const double2* g = a.g + (size_t)r * (m + 1);
+  for (int i = k - 1; i >= 0; i--) {
+    cplx<double> acc = zc2(g[i]);
+    for (int l = i + 1; l < k; l++) acc = acc - zc2(H[(size_t)i * m + l]) * zc2(y[(size_t)l * R + r]);
+    cplx<double> d = zc2(H[(size_t)i * m + i]);
+    double dn = norm2(d);
+    cplx<double> q = dn > 0 ? acc * cplx<double>(d.re / dn, -d.im / dn) : cplx<double>(0, 0);
+    y[(size_t)i * R + r] = zd2(q);
+  }
+}
+
+void launch_arnoldi_start(const ArnoldiDev& a, const double2* nr2, cudaStream_t st) {
+  k_arnoldi_start<<<(a.R + 63) / 64, 64, 0, st>>>(a, nr2);
+  CKL("arnoldi_start");
+}
+void launch_arnoldi_step(const ArnoldiDev& a, int j, const double2* h, const double2* h2, const double2* hn2,
+                         cudaStream_t st) {
+  ScopedTimer timer_("arnoldi", st);
+  k_arnoldi_step<<<(a.R + 63) / 64, 64, 0, st>>>(a, j, h, h2, hn2);
+  CKL("arnoldi_step");
+}
+void launch_arnoldi_solve(const ArnoldiDev& a, int k, double2* y, cudaStream_t st) {
+  k_arnoldi_solve<<<(a.R + 63) / 64, 64, 0, st>>>(a, k, y);
+  CKL("arnoldi_solve");
 }
 
 void launch_field_convert(const FineGeom& g, int pin, const void* in, const float* inn, int pout, void* out, float* outn,

@@ -40,10 +40,37 @@ struct Blas {
   // y(., r) = a[r] x(., r) + b[r] y(., r); a zero coefficient skips reading its operand
   void axpby(const double2* a_host, const VSet& x, const double2* b_host, const VSet& y);
 
+  // device-result variants: no host synchronisation, coefficients and results
+  // stay in device memory (layouts as above)
+  void dots_dev(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_dev);
+  void maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev, double sign,
+                 double2* norms2_dev);
+  // y(., r) = a[r] x(., r), a in device memory
+  void scale_dev(const double2* a_dev, const VSet& x, const VSet& y);
+
   // single-vector conveniences (R = 1)
   double norm2(const void* a, int t, size_t n);
   void axpby(double2 a, const void* x, int tx, double2 b, void* y, int ty, size_t n);
 };
+
+// Arnoldi bookkeeping on the device for R lockstep GMRES systems (Givens
+// rotations as in the host code: G = [[conj(c), conj(s)], [-s, c]]).
+// State per system r: H[(r*(m+1) + i)*m + j], cs/sn[r*m + i], g[r*(m+1) + i].
+struct ArnoldiDev {
+  double2 *H, *cs, *sn, *g;
+  double* bn;      // ||b_r||
+  double* est;     // residual estimate / ||b_r||
+  double2* scale;  // 1 / norm for the next basis vector (0 if the norm vanished)
+  int m, R;
+};
+// start of a cycle from the squared residual norms nr2[r].x
+void launch_arnoldi_start(const ArnoldiDev& a, const double2* nr2, cudaStream_t st);
+// column j from the Gram-Schmidt coefficients h (+ h2 if non-null), [i*R + r],
+// and the squared norm of the orthogonalised vector hn2[r].x
+void launch_arnoldi_step(const ArnoldiDev& a, int j, const double2* h, const double2* h2, const double2* hn2,
+                         cudaStream_t st);
+// y[i*R + r] from the triangular systems of the first k columns
+void launch_arnoldi_solve(const ArnoldiDev& a, int k, double2* y, cudaStream_t st);
 
 void launch_field_convert(const FineGeom& g, int pin, const void* in, const float* inn, int pout, void* out, float* outn,
                           cudaStream_t st);

@@ -140,6 +140,12 @@ struct ddtm_ctx {
   double setup_mu = 0;
   double setup_s = 0;
   ddtm::ScratchPool scratch;
+  // pinned host scratch and named event pairs (created on first use, kept)
+  std::map<std::string, std::pair<void*, size_t>> host_bufs;
+  std::map<std::string, std::pair<cudaEvent_t, cudaEvent_t>> event_pairs;
+  void* scratch_host(const std::string& name, size_t bytes);
+  void events(const std::string& name, cudaEvent_t ev[2]);
+  ~ddtm_ctx();
 };
 
 namespace ddtm {

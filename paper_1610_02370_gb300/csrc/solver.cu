@@ -132,10 +132,14 @@ typedef std::function<void(cplx<float>*, const cplx<float>*)> OpF32;
 // vectors of L entries each, interleaved; FP64 inner products).  Every
 // iteration orthogonalises all R Krylov vectors with one multi-dot and one
 // fused multi-axpy + norm (classical Gram-Schmidt; a second pass when tol is
-// below 1e-3), keeps each system's Hessenberg matrix and Givens rotations on
-// the host, and stops when every system's residual estimate is below tol
-// (systems with b_r = 0 count as solved with x_r = 0).  x is overwritten
-// (zero start).  Returns the iteration count; relres[r] the estimates.
+// below 1e-3).  The Hessenberg matrices, Givens rotations and least-squares
+// updates stay on the device, so an iteration issues kernels only; the host
+// reads the residual estimates one iteration behind (asynchronous copy and an
+// event) and stops when every system is below tol (systems with b_r = 0 count
+// as solved with x_r = 0).  An iteration already issued when the stop is seen
+// is discarded: the solution uses exactly the columns up to the converged one.
+// x is overwritten (zero start).  Returns the iteration count; relres[r] the
+// final estimates.
 static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float>* b, size_t L, int R, int m, int max_restarts,
                    double tol, double* relres, const char* tag) {
   Blas B(c->stream, &c->scratch, &c->ring);
@@ -143,23 +147,54 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
   const size_t N = L * R;
   cplx<float>* V = (cplx<float>*)c->scratch.get(t + "_V", (size_t)(m + 1) * N * sizeof(float2));
   cplx<float>* w = (cplx<float>*)c->scratch.get(t + "_w", N * sizeof(float2));
+  // device bookkeeping, one block of scratch
+  size_t nH = (size_t)R * (m + 1) * m, ncs = (size_t)R * m, ng = (size_t)R * (m + 1), nh = (size_t)(m + 1) * R;
+  size_t tot2 = nH + 2 * ncs + ng + 3 * nh + 3 * (size_t)R;
+  double2* st2 = (double2*)c->scratch.get(t + "_state", tot2 * sizeof(double2) + 2 * (size_t)R * sizeof(double));
+  ArnoldiDev ad;
+  ad.H = st2;
+  ad.cs = ad.H + nH;
+  ad.sn = ad.cs + ncs;
+  ad.g = ad.sn + ncs;
+  double2* h = ad.g + ng;
+  double2* h2 = h + nh;
+  double2* y = h2 + nh;
+  double2* nr2 = y + nh;
+  ad.scale = nr2 + R;
+  double2* unused = ad.scale + R;
+  (void)unused;
+  ad.bn = (double*)(st2 + tot2);
+  ad.est = ad.bn + R;
+  ad.m = m;
+  ad.R = R;
+  // pinned mirrors of the estimates, double-buffered by iteration parity
+  double* est_h = (double*)c->scratch_host(t + "_est", 2 * (size_t)R * sizeof(double));
+  cudaEvent_t ev[2];
+  c->events(t, ev);
+
   CK(cudaMemsetAsync(x, 0, N * sizeof(float2), c->stream));
   auto vs = [&](const void* p) { return VSet{(void*)p, 1, L, R, true}; };
-  std::vector<double> bn(R), beta(R), hn2(R), est(R, 0.0);
+  std::vector<double> bn(R);
   B.norms2(vs(b), bn.data());
   for (int r = 0; r < R; r++) bn[r] = sqrt(bn[r]);
+  CK(cudaMemcpyAsync(ad.bn, bn.data(), R * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   const bool reorth = tol < 1e-3;
-  std::vector<zc> H((size_t)R * (m + 1) * m), cs((size_t)R * m), sn((size_t)R * m), g((size_t)R * (m + 1));
-  std::vector<double2> h((size_t)(m + 1) * R), h2((size_t)(m + 1) * R), coef(R), zero(R, make_double2(0, 0)),
-      one(R, make_double2(1, 0)), mone(R, make_double2(-1, 0));
-  auto Hat = [&](int r, int i, int j) -> zc& { return H[((size_t)r * (m + 1) + i) * m + j]; };
-  auto all_done = [&]() {
-    for (int r = 0; r < R; r++)
-      if (bn[r] > 0 && !(est[r] <= tol)) return false;
+  std::vector<double2> one(R, make_double2(1, 0)), mone(R, make_double2(-1, 0));
+  std::vector<double> est(R, 0.0);
+  auto all_done = [&](const double* e) {
+    for (int r = 0; r < R; r++) {
+      if (!std::isfinite(e[r])) throw Error(DDTM_ERR_NAN, "non-finite residual in GMRES (" + t + ")");
+      if (bn[r] > 0 && !(e[r] <= tol)) return false;
+    }
     return true;
   };
+  auto fetch_est = [&](int slot) {
+    CK(cudaMemcpyAsync(est_h + (size_t)slot * R, ad.est, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(ev[slot], c->stream));
+  };
   int iters = 0;
-  for (int cyc = 0; cyc <= max_restarts; cyc++) {
+  bool done = false;
+  for (int cyc = 0; cyc <= max_restarts && !done; cyc++) {
     if (cyc == 0) {
       CK(cudaMemcpyAsync(V, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
     } else {
@@ -167,68 +202,47 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
       CK(cudaMemcpyAsync(V, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
       B.axpby(mone.data(), vs(w), one.data(), vs(V));
     }
-    B.norms2(vs(V), beta.data());
-    for (int r = 0; r < R; r++) {
-      beta[r] = sqrt(beta[r]);
-      est[r] = bn[r] > 0 ? beta[r] / bn[r] : 0.0;
-      if (!std::isfinite(est[r])) throw Error(DDTM_ERR_NAN, "non-finite residual in GMRES (" + t + ")");
-      coef[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
-    }
-    if (all_done()) break;
-    B.axpby(zero.data(), vs(V), coef.data(), vs(V));
-    std::fill(g.begin(), g.end(), zc(0));
-    for (int r = 0; r < R; r++) g[(size_t)r * (m + 1)] = beta[r];
+    B.dots_dev(vs(V), 0, 1, vs(V), nr2);
+    launch_arnoldi_start(ad, nr2, c->stream);
+    fetch_est(0);
+    CK(cudaEventSynchronize(ev[0]));
+    for (int r = 0; r < R; r++) est[r] = est_h[r];
+    if (all_done(est.data())) break;
+    B.scale_dev(ad.scale, vs(V), vs(V));
     int k = 0;
     for (int j = 0; j < m; j++) {
       A(w, V + (size_t)j * N);
-      B.dots(vs(V), N, j + 1, vs(w), h.data());
-      B.maxpy(vs(w), vs(V), N, j + 1, h.data(), -1.0, reorth ? nullptr : hn2.data());
+      B.dots_dev(vs(V), N, j + 1, vs(w), h);
+      B.maxpy_dev(vs(w), vs(V), N, j + 1, h, -1.0, reorth ? nullptr : nr2);
       if (reorth) {
-        B.dots(vs(V), N, j + 1, vs(w), h2.data());
-        B.maxpy(vs(w), vs(V), N, j + 1, h2.data(), -1.0, hn2.data());
-        for (size_t q = 0; q < h.size(); q++) { h[q].x += h2[q].x; h[q].y += h2[q].y; }
+        B.dots_dev(vs(V), N, j + 1, vs(w), h2);
+        B.maxpy_dev(vs(w), vs(V), N, j + 1, h2, -1.0, nr2);
       }
-      for (int r = 0; r < R; r++) {
-        double hn = sqrt(hn2[r]);
-        for (int i = 0; i <= j; i++) Hat(r, i, j) = zc(h[(size_t)i * R + r].x, h[(size_t)i * R + r].y);
-        Hat(r, j + 1, j) = hn;
-        for (int i = 0; i < j; i++) {
-          zc a = Hat(r, i, j), bb = Hat(r, i + 1, j);
-          Hat(r, i, j) = std::conj(cs[(size_t)r * m + i]) * a + std::conj(sn[(size_t)r * m + i]) * bb;
-          Hat(r, i + 1, j) = -sn[(size_t)r * m + i] * a + cs[(size_t)r * m + i] * bb;
-        }
-        zc a = Hat(r, j, j);
-        double rho = sqrt(std::norm(a) + hn * hn);
-        cs[(size_t)r * m + j] = rho > 0 ? a / rho : zc(1);
-        sn[(size_t)r * m + j] = rho > 0 ? zc(hn / rho) : zc(0);
-        Hat(r, j, j) = rho;
-        Hat(r, j + 1, j) = 0;
-        zc* gr = &g[(size_t)r * (m + 1)];
-        gr[j + 1] = -sn[(size_t)r * m + j] * gr[j];
-        gr[j] = std::conj(cs[(size_t)r * m + j]) * gr[j];
-        est[r] = bn[r] > 0 ? std::abs(gr[j + 1]) / bn[r] : 0.0;
-        if (!std::isfinite(est[r])) throw Error(DDTM_ERR_NAN, "non-finite residual estimate in GMRES (" + t + ")");
-        coef[r] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0);
-      }
-      k = j + 1;
+      launch_arnoldi_step(ad, j, h, reorth ? h2 : nullptr, nr2, c->stream);
+      fetch_est(j & 1);
+      if (j < m - 1) B.scale_dev(ad.scale, vs(w), vs(V + (size_t)(j + 1) * N));  // V_{j+1} = w / ||w||
       iters++;
-      if (all_done() || j == m - 1) break;
-      B.axpby(coef.data(), vs(w), zero.data(), vs(V + (size_t)(j + 1) * N));  // V_{j+1} = w / hn
-    }
-    // x += V y per system, y from the triangular systems (zero where a pivot vanished)
-    std::vector<double2> yc((size_t)k * R);
-    for (int r = 0; r < R; r++) {
-      std::vector<zc> y(k);
-      for (int i = k - 1; i >= 0; i--) {
-        zc sacc = g[(size_t)r * (m + 1) + i];
-        for (int l = i + 1; l < k; l++) sacc -= Hat(r, i, l) * y[l];
-        zc d = Hat(r, i, i);
-        y[i] = std::abs(d) > 0 ? sacc / d : zc(0);
+      k = j + 1;
+      if (j >= 1) {  // estimates of the previous iteration
+        CK(cudaEventSynchronize(ev[(j - 1) & 1]));
+        const double* e = est_h + (size_t)((j - 1) & 1) * R;
+        if (all_done(e)) {
+          for (int r = 0; r < R; r++) est[r] = e[r];
+          k = j;  // iteration j is discarded
+          iters--;
+          done = true;
+          break;
+        }
       }
-      for (int i = 0; i < k; i++) yc[(size_t)i * R + r] = make_double2(y[i].real(), y[i].imag());
     }
-    B.maxpy(vs(x), vs(V), N, k, yc.data(), +1.0, nullptr);
-    if (all_done()) break;
+    if (!done) {
+      CK(cudaEventSynchronize(ev[(k - 1) & 1]));
+      const double* e = est_h + (size_t)((k - 1) & 1) * R;
+      for (int r = 0; r < R; r++) est[r] = e[r];
+      done = all_done(est.data());
+    }
+    launch_arnoldi_solve(ad, k, y, c->stream);
+    B.maxpy_dev(vs(x), vs(V), N, k, y, +1.0, nullptr);
   }
   for (int r = 0; r < R; r++) relres[r] = est[r];
   return iters;
@@ -287,15 +301,18 @@ void mg_precondition(ddtm_ctx* c, int prec, void* z, float* zn, const void* v, c
   sap_run(c, prec, z, zn, v, vn, mu, c->p.post_smooth, c->p.nmr, false, R);
 }
 
-// ---- outer flexible GMRES in FP64 (Sec. 2.5) --------------------------------------------
-// R systems in lockstep.  The Arnoldi basis V and all orthogonalisation are
-// FP64 (classical Gram-Schmidt, two passes); Z_j = M v_j is stored in the
-// smoother precision (a flexible method takes Z_j as it is: w = D Z_j is
-// applied to exactly the stored Z_j, and x is updated with the same Z_j).  A
-// cycle ends at the restart length, when every residual estimate is below the
-// target, or when every estimate dropped below restart_tol times its cycle's
-// starting residual (Table 1: mixed-precision restart criterion); every cycle
-// starts from the true FP64 residual b - D x.
+// ---- outer mixed-precision flexible GMRES (Sec. 2.5, Table 1) ---------------------------
+// R systems in lockstep, as iterative refinement around an FP32 flexible GMRES
+// cycle: every cycle starts from the true FP64 residual r = b - D x (FP64
+// operator), runs flexible GMRES on r with the Arnoldi basis, the operator
+// applications w = D z and the Gram-Schmidt products in FP32 (inner products
+// summed in FP64), and ends with the FP64 update x += sum_j y_j Z_j.  A cycle
+// stops when every system's estimate fell below restart_tol times its
+// starting residual (Table 1's mixed-precision restarting criterion) or
+// below the final target, or at the restart length.  Z_j = M v_j is stored in
+// the smoother precision: the flexible method uses exactly the stored Z_j for
+// both w = D Z_j and the update.  Hessenberg matrices and Givens rotations stay
+// on the device; the host reads the estimates one iteration behind.
 struct OuterResult {
   int iters = 0, restarts = 0;
   std::vector<double> relres;
@@ -306,123 +323,166 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
   const FineGeom& g = c->g;
   const ddtm_params& p = c->p;
   Blas B(c->stream, &c->scratch, &c->ring);
-  int sp = p.smoother_prec, m = p.outer_restart;
+  const int sp = p.smoother_prec, m = p.outer_restart;
   const size_t n = (size_t)g.V * 12;  // complex entries of one fine field
-  const size_t fb = fine_field_bytes(g, sp);
-  double* V = (double*)c->scratch.get("out_V", (size_t)(m + 1) * R * n * 16);
+  const size_t fb = fine_field_bytes(g, sp), f32 = n * 8;
+  ensure_fine_prec(c, PREC_F32);
+  float2* V = (float2*)c->scratch.get("out_V", (size_t)(m + 1) * R * f32);
   char* Z = (char*)c->scratch.get("out_Z", (size_t)m * R * fb);
   float* Zn = (float*)c->scratch.get("out_Zn", (size_t)m * R * g.V * sizeof(float));
-  double* w = (double*)c->scratch.get("out_w", (size_t)R * n * 16);
-  double* t64 = (double*)c->scratch.get("out_t64", (size_t)R * n * 16);
+  float2* w = (float2*)c->scratch.get("out_w", (size_t)R * f32);
+  float2* t32 = (float2*)c->scratch.get("out_t32", (size_t)R * f32);
+  double* r64 = (double*)c->scratch.get("out_r64", (size_t)R * n * 16);
   char* vsb = (char*)c->scratch.get("out_vs", (size_t)R * fb);
   float* vsn = (float*)c->scratch.get("out_vsn", (size_t)R * g.V * sizeof(float));
-  auto Zj = [&](int j, int r) { return (void*)(Z + ((size_t)j * R + r) * fb); };
-  auto Zjn = [&](int j, int r) { return sp == PREC_F16 ? Zn + ((size_t)j * R + r) * g.V : (float*)nullptr; };
-  auto Vj = [&](int j) { return V + 2 * (size_t)j * R * n; };
-  auto set = [&](const double* p0) { return VSet{(void*)p0, 0, n, R, false}; };
+  auto Zj = [&](int j) { return (void*)(Z + (size_t)j * R * fb); };
+  auto Zjn = [&](int j) { return sp == PREC_F16 ? Zn + (size_t)j * R * g.V : (float*)nullptr; };
+  auto Vj = [&](int j) { return V + (size_t)j * R * n; };
+  auto s64 = [&](const double* p0) { return VSet{(void*)p0, 0, n, R, false}; };
+  auto s32 = [&](const float2* p0) { return VSet{(void*)p0, 1, n, R, false}; };
   auto D64 = [&](double* out, const double* in) {
     for (int r = 0; r < R; r++)
       launch_dslash(g, PREC_F64, out + 2 * (size_t)r * n, nullptr, in + 2 * (size_t)r * n, nullptr, c->links[0].p,
                     c->clover[0].p, mu, c->stream);
   };
+  auto D32 = [&](float2* out, const float2* in) {
+    for (int r = 0; r < R; r++)
+      launch_dslash(g, PREC_F32, out + (size_t)r * n, nullptr, in + (size_t)r * n, nullptr, c->links[PREC_F32].p,
+                    c->clover[PREC_F32].p, mu, c->stream);
+  };
+  // device bookkeeping
+  size_t nH = (size_t)R * (m + 1) * m, ncs = (size_t)R * m, ng = (size_t)R * (m + 1), nh = (size_t)(m + 1) * R;
+  size_t tot2 = nH + 2 * ncs + ng + 3 * nh + 2 * (size_t)R;
+  double2* st2 = (double2*)c->scratch.get("out_state", tot2 * sizeof(double2) + 2 * (size_t)R * sizeof(double));
+  ArnoldiDev ad;
+  ad.H = st2;
+  ad.cs = ad.H + nH;
+  ad.sn = ad.cs + ncs;
+  ad.g = ad.sn + ncs;
+  double2* h = ad.g + ng;
+  double2* h2 = h + nh;
+  double2* y = h2 + nh;
+  double2* nr2 = y + nh;
+  ad.scale = nr2 + R;
+  ad.bn = (double*)(st2 + tot2);
+  ad.est = ad.bn + R;
+  ad.m = m;
+  ad.R = R;
+  double* est_h = (double*)c->scratch_host("out_est", 2 * (size_t)R * sizeof(double));
+  cudaEvent_t ev[2];
+  c->events("out", ev);
+
   OuterResult res;
   res.relres.assign(R, 1.0);
-  std::vector<double> bn(R), beta(R), hn2(R), est(R);
-  B.norms2(set(b), bn.data());
+  std::vector<double> bn(R), beta(R), thr(R);
+  B.norms2(s64(b), bn.data());
   for (int r = 0; r < R; r++) bn[r] = sqrt(bn[r]);
   CK(cudaMemsetAsync(x, 0, (size_t)R * n * 16, c->stream));
-  std::vector<zc> H((size_t)R * (m + 1) * m), cs((size_t)R * m), sn((size_t)R * m), gv((size_t)R * (m + 1));
-  std::vector<double2> h((size_t)(m + 1) * R), h2((size_t)(m + 1) * R), coef(R), zero(R, make_double2(0, 0)),
-      one(R, make_double2(1, 0)), mone(R, make_double2(-1, 0));
-  auto Hat = [&](int r, int i, int j) -> zc& { return H[((size_t)r * (m + 1) + i) * m + j]; };
+  std::vector<double2> one(R, make_double2(1, 0)), mone(R, make_double2(-1, 0)), zero(R, make_double2(0, 0)), sc(R);
+  auto fetch_est = [&](int slot) {
+    CK(cudaMemcpyAsync(est_h + (size_t)slot * R, ad.est, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(ev[slot], c->stream));
+  };
+  auto cycle_done = [&](const double* e) {
+    for (int r = 0; r < R; r++) {
+      if (!std::isfinite(e[r])) throw Error(DDTM_ERR_NAN, "non-finite outer residual estimate");
+      if (!(e[r] <= thr[r])) return false;
+    }
+    return true;
+  };
   bool first = true;
   while (true) {
-    if (first) {
-      CK(cudaMemcpyAsync(Vj(0), b, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->stream));
-    } else {
-      D64(w, x);
-      CK(cudaMemcpyAsync(Vj(0), b, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->stream));
-      B.axpby(mone.data(), set(w), one.data(), set(Vj(0)));
+    // true residual in FP64
+    CK(cudaMemcpyAsync(r64, b, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->stream));
+    if (!first) {
+      double* t64 = (double*)c->scratch.get("out_t64", (size_t)R * n * 16);
+      D64(t64, x);
+      B.axpby(mone.data(), s64(t64), one.data(), s64(r64));
       res.restarts++;
     }
     first = false;
-    B.norms2(set(Vj(0)), beta.data());
+    B.norms2(s64(r64), beta.data());
     bool done = true;
     for (int r = 0; r < R; r++) {
       beta[r] = sqrt(beta[r]);
       res.relres[r] = bn[r] > 0 ? beta[r] / bn[r] : 0.0;
       if (!std::isfinite(res.relres[r])) throw Error(DDTM_ERR_NAN, "non-finite outer residual");
       done = done && res.relres[r] <= p.outer_tol;
-      coef[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
+      sc[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
+      // stop the cycle at restart_tol relative to its start, or at the final target
+      thr[r] = beta[r] > 0 ? std::max(p.restart_tol, 0.5 * p.outer_tol * bn[r] / beta[r]) : 1.0;
     }
     if (done) {
       res.converged = true;
       break;
     }
     if (res.iters >= p.outer_max_iters) break;
-    B.axpby(zero.data(), set(Vj(0)), coef.data(), set(Vj(0)));
-    std::fill(gv.begin(), gv.end(), zc(0));
-    for (int r = 0; r < R; r++) gv[(size_t)r * (m + 1)] = beta[r];
+    // V_0 = r / beta in FP32; the device Arnoldi state starts from ||V_0|| (= 1)
+    // V_0 = r / beta in FP32; the device state starts with g_0 = beta and
+    // estimates relative to beta (so y is the correction for r itself)
+    B.axpby(sc.data(), s64(r64), zero.data(), s32(Vj(0)));
+    {
+      double* hb = (double*)c->scratch_host("out_beta", 3 * (size_t)R * sizeof(double));
+      for (int r = 0; r < R; r++) {
+        hb[r] = beta[r] > 0 ? beta[r] : 1.0;       // bn: reference of the estimates
+        hb[R + 2 * r] = beta[r] * beta[r];         // nr2[r].x
+        hb[R + 2 * r + 1] = 0.0;                   // nr2[r].y
+      }
+      CK(cudaMemcpyAsync(ad.bn, hb, R * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(nr2, hb + R, 2 * (size_t)R * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      launch_arnoldi_start(ad, nr2, c->stream);
+      CK(cudaStreamSynchronize(c->stream));  // the pinned block is rewritten next cycle
+    }
     int k = 0;
+    bool cyc_done = false;
     for (int j = 0; j < m; j++) {
-      for (int r = 0; r < R; r++)
-        launch_field_convert(g, PREC_F64, Vj(j) + 2 * (size_t)r * n, nullptr, sp, vsb + (size_t)r * fb,
-                             sp == PREC_F16 ? vsn + (size_t)r * g.V : nullptr, c->stream);
-      mg_precondition(c, sp, Zj(j, 0), Zjn(j, 0), vsb, sp == PREC_F16 ? vsn : nullptr, mu, R);
-      for (int r = 0; r < R; r++)
-        launch_field_convert(g, sp, Zj(j, r), Zjn(j, r), PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
-      D64(w, t64);
-      B.dots(set(V), (size_t)R * n, j + 1, set(w), h.data());
-      B.maxpy(set(w), set(V), (size_t)R * n, j + 1, h.data(), -1.0, nullptr);
-      B.dots(set(V), (size_t)R * n, j + 1, set(w), h2.data());
-      B.maxpy(set(w), set(V), (size_t)R * n, j + 1, h2.data(), -1.0, hn2.data());
-      bool stop = true;
-      for (int r = 0; r < R; r++) {
-        double hn = sqrt(hn2[r]);
-        for (int i = 0; i <= j; i++)
-          Hat(r, i, j) = zc(h[(size_t)i * R + r].x + h2[(size_t)i * R + r].x, h[(size_t)i * R + r].y + h2[(size_t)i * R + r].y);
-        Hat(r, j + 1, j) = hn;
-        for (int i = 0; i < j; i++) {
-          zc a = Hat(r, i, j), bb = Hat(r, i + 1, j);
-          Hat(r, i, j) = std::conj(cs[(size_t)r * m + i]) * a + std::conj(sn[(size_t)r * m + i]) * bb;
-          Hat(r, i + 1, j) = -sn[(size_t)r * m + i] * a + cs[(size_t)r * m + i] * bb;
-        }
-        zc a = Hat(r, j, j);
-        double rho = sqrt(std::norm(a) + hn * hn);
-        cs[(size_t)r * m + j] = rho > 0 ? a / rho : zc(1);
-        sn[(size_t)r * m + j] = rho > 0 ? zc(hn / rho) : zc(0);
-        Hat(r, j, j) = rho;
-        Hat(r, j + 1, j) = 0;
-        zc* gr = &gv[(size_t)r * (m + 1)];
-        gr[j + 1] = -sn[(size_t)r * m + j] * gr[j];
-        gr[j] = std::conj(cs[(size_t)r * m + j]) * gr[j];
-        est[r] = std::abs(gr[j + 1]);
-        if (!std::isfinite(est[r])) throw Error(DDTM_ERR_NAN, "non-finite outer residual estimate");
-        bool ok = bn[r] == 0 || est[r] <= p.outer_tol * bn[r] || est[r] <= p.restart_tol * beta[r] || hn == 0;
-        stop = stop && ok;
-        coef[r] = make_double2(hn > 0 ? 1.0 / hn : 0.0, 0);
+      const void* vin = Vj(j);
+      const float* vinn = nullptr;
+      if (sp != PREC_F32) {
+        for (int r = 0; r < R; r++)
+          launch_field_convert(g, PREC_F32, Vj(j) + (size_t)r * n, nullptr, sp, vsb + (size_t)r * fb,
+                               sp == PREC_F16 ? vsn + (size_t)r * g.V : nullptr, c->stream);
+        vin = vsb;
+        vinn = sp == PREC_F16 ? vsn : nullptr;
       }
-      k = j + 1;
+      mg_precondition(c, sp, Zj(j), Zjn(j), vin, vinn, mu, R);
+      const float2* zin = (const float2*)Zj(j);
+      if (sp != PREC_F32) {
+        for (int r = 0; r < R; r++)
+          launch_field_convert(g, sp, (char*)Zj(j) + (size_t)r * fb, sp == PREC_F16 ? Zjn(j) + (size_t)r * g.V : nullptr,
+                               PREC_F32, t32 + (size_t)r * n, nullptr, c->stream);
+        zin = t32;
+      }
+      D32(w, zin);
+      B.dots_dev(s32(V), (size_t)R * n, j + 1, s32(w), h);
+      B.maxpy_dev(s32(w), s32(V), (size_t)R * n, j + 1, h, -1.0, nullptr);
+      B.dots_dev(s32(V), (size_t)R * n, j + 1, s32(w), h2);
+      B.maxpy_dev(s32(w), s32(V), (size_t)R * n, j + 1, h2, -1.0, nr2);
+      launch_arnoldi_step(ad, j, h, h2, nr2, c->stream);
+      fetch_est(j & 1);
+      if (j < m - 1) B.scale_dev(ad.scale, s32(w), s32(Vj(j + 1)));
       res.iters++;
-      if (stop || res.iters >= p.outer_max_iters || j == m - 1) break;
-      B.axpby(coef.data(), set(w), zero.data(), set(Vj(j + 1)));  // V_{j+1} = w / hn
-    }
-    // x += sum_j y_j Z_j per system
-    std::vector<std::vector<zc>> ys(R, std::vector<zc>(k));
-    for (int r = 0; r < R; r++) {
-      for (int i = k - 1; i >= 0; i--) {
-        zc sacc = gv[(size_t)r * (m + 1) + i];
-        for (int l = i + 1; l < k; l++) sacc -= Hat(r, i, l) * ys[r][l];
-        zc d = Hat(r, i, i);
-        ys[r][i] = std::abs(d) > 0 ? sacc / d : zc(0);
+      k = j + 1;
+      if (j >= 1) {
+        CK(cudaEventSynchronize(ev[(j - 1) & 1]));
+        if (cycle_done(est_h + (size_t)((j - 1) & 1) * R)) {
+          k = j;  // iteration j is discarded
+          res.iters--;
+          cyc_done = true;
+          break;
+        }
       }
+      if (res.iters >= p.outer_max_iters) break;
     }
+    if (!cyc_done) CK(cudaEventSynchronize(ev[(k - 1) & 1]));
+    launch_arnoldi_solve(ad, k, y, c->stream);
+    // x += sum_j y_j Z_j in FP64
+    double* t64 = (double*)c->scratch.get("out_t64", (size_t)R * n * 16);
     for (int j = 0; j < k; j++) {
-      for (int r = 0; r < R; r++) {
-        launch_field_convert(g, sp, Zj(j, r), Zjn(j, r), PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
-        coef[r] = make_double2(ys[r][j].real(), ys[r][j].imag());
-      }
-      B.axpby(coef.data(), set(t64), one.data(), set(x));
+      for (int r = 0; r < R; r++)
+        launch_field_convert(g, sp, (char*)Zj(j) + (size_t)r * fb, sp == PREC_F16 ? Zjn(j) + (size_t)r * g.V : nullptr,
+                             PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
+      B.maxpy_dev(s64(x), s64(t64), 0, 1, y + (size_t)j * R, +1.0, nullptr);
     }
   }
   return res;

@@ -29,7 +29,8 @@ __device__ __forceinline__ void cta_sum2d(double& a, double& b, double* red) {
 
 // Gather the chirality-s halves of nv test vectors (FP32 fine fields, internal
 // layout, field stride 12*V) into P and orthonormalise each aggregate half by
-// modified Gram-Schmidt in index order, twice; inner products in FP64.
+// modified Gram-Schmidt in index order, twice.  Each thread keeps its site's 6
+// components in FP32; the CTA-wide inner products are summed in FP64.
 // One CTA per (blk, s); thread = site loc.
 __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv, int nv, int Vb, long V) {
   __shared__ double red[64];
@@ -44,37 +45,36 @@ __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv,
   __syncthreads();
   for (int sweep = 0; sweep < 2; sweep++) {
     for (int i = 0; i < nv; i++) {
-      double2 vi[6];
+      float2 vi[6];
       if (act)
-        for (int comp = 0; comp < 6; comp++) {
-          float2 a = P[pidx(blk, s, i, comp, loc, nv, Vb)];
-          vi[comp] = make_double2(a.x, a.y);
-        }
+        for (int comp = 0; comp < 6; comp++) vi[comp] = P[pidx(blk, s, i, comp, loc, nv, Vb)];
       for (int j = 0; j < i; j++) {
-        double re = 0, im = 0;
-        double2 vj[6];
+        float pre = 0, pim = 0;
+        float2 vj[6];
         if (act)
           for (int comp = 0; comp < 6; comp++) {
-            float2 a = P[pidx(blk, s, j, comp, loc, nv, Vb)];
-            vj[comp] = make_double2(a.x, a.y);
-            re += vj[comp].x * vi[comp].x + vj[comp].y * vi[comp].y;  // <v_j, v_i>
-            im += vj[comp].x * vi[comp].y - vj[comp].y * vi[comp].x;
+            vj[comp] = P[pidx(blk, s, j, comp, loc, nv, Vb)];
+            pre += vj[comp].x * vi[comp].x + vj[comp].y * vi[comp].y;  // <v_j, v_i>
+            pim += vj[comp].x * vi[comp].y - vj[comp].y * vi[comp].x;
           }
+        double re = pre, im = pim;
         cta_sum2d(re, im, red);
+        const float fre = (float)re, fim = (float)im;
         if (act)
           for (int comp = 0; comp < 6; comp++) {
-            vi[comp].x -= re * vj[comp].x - im * vj[comp].y;
-            vi[comp].y -= re * vj[comp].y + im * vj[comp].x;
+            vi[comp].x -= fre * vj[comp].x - fim * vj[comp].y;
+            vi[comp].y -= fre * vj[comp].y + fim * vj[comp].x;
           }
       }
-      double nn = 0, dummy = 0;
+      float pn = 0;
       if (act)
-        for (int comp = 0; comp < 6; comp++) nn += vi[comp].x * vi[comp].x + vi[comp].y * vi[comp].y;
+        for (int comp = 0; comp < 6; comp++) pn += vi[comp].x * vi[comp].x + vi[comp].y * vi[comp].y;
+      double nn = pn, dummy = 0;
       cta_sum2d(nn, dummy, red);
-      double inv = nn > 0 ? 1.0 / sqrt(nn) : 0.0;
+      const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
       if (act)
         for (int comp = 0; comp < 6; comp++)
-          P[pidx(blk, s, i, comp, loc, nv, Vb)] = make_float2((float)(vi[comp].x * inv), (float)(vi[comp].y * inv));
+          P[pidx(blk, s, i, comp, loc, nv, Vb)] = make_float2(vi[comp].x * inv, vi[comp].y * inv);
       __syncthreads();
     }
   }
