@@ -42,7 +42,11 @@ WORKLOADS = {
     "24x24x24x48": dict(dims=(48, 24, 24, 24), eps=0.15, kappa=0.1370, c_sw=1.5755, mu=0.002),
     "16x16x16x32": dict(dims=(32, 16, 16, 16), eps=0.2, kappa=0.1340, c_sw=1.5755, mu=0.003),
 }
-MG = dict(block=(4, 4, 4, 4), nv=24, n_setup=6, post_smooth=4, nmr=3, outer_restart=30, outer_tol=1e-10,
+# Post-smoothing: Table 1 uses 4 SAP cycles, tuned for the real ensemble cA2.09.48.  On these synthetic
+# fields the mass lies well below critical and SAP amplifies smooth modes, so the cycle count is tuned as
+# the paper does per ensemble: at 24^3x48 one setup then single-rhs solves gave 4 cycles: no convergence
+# in 120 iterations; 2 cycles: 22 iterations; 1 cycle: 27 (parameter study recorded with the design notes).
+MG = dict(block=(4, 4, 4, 4), nv=24, n_setup=6, post_smooth=2, nmr=3, outer_restart=30, outer_tol=1e-10,
           smoother_prec=2, coarse_prec=1)
 NRHS = 12
 SEED = 2024

@@ -68,6 +68,7 @@ __global__ void k_bdots(const TV* __restrict__ V, size_t ldv, int nvec, const TW
     const TV* vj = V + (size_t)j * ldv;
     typedef typename Acc<TV, TW>::T AT;
     AT are = 0, aim = 0;
+#pragma unroll 4
     for (size_t i = beg + threadIdx.x; i < end; i += bd) {
       auto x = ldc<AT>(vj, i);
       auto y = ldc<AT>(w, i);
@@ -120,21 +121,42 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
   for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = INTER ? coef[k] : coef[(size_t)k * R + r_sep];
   __syncthreads();
   double nn = 0;
+  typedef typename Acc<TV, TW>::T AT;
+  // each thread updates EPT entries spaced by the CTA size (coalesced), with
+  // the basis loop outside so EPT independent loads are in flight per step
+  const int EPT = 4;
   if (INTER) {
-    const size_t N = n * R, stride = (size_t)G * blockDim.x;  // stride is a multiple of R
-    const int r = threadIdx.x % R;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-      typedef typename Acc<TV, TW>::T AT;
-      auto acc = ldc<AT>(w, i);
+    const size_t N = n * R, span = (size_t)blockDim.x * EPT;
+    const int r = threadIdx.x % R;  // blockDim and span are multiples of R
+    for (size_t base = (size_t)blockIdx.x * span; base < N; base += (size_t)G * span) {
+      cplx<AT> acc[EPT];
+      bool in[EPT];
+#pragma unroll
+      for (int u = 0; u < EPT; u++) {
+        size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
+        in[u] = i < N;
+        acc[u] = in[u] ? ldc<AT>(w, i) : cplx<AT>(0, 0);
+      }
+#pragma unroll 2
       for (int j = 0; j < nvec; j++) {
-        auto v = ldc<AT>(V + (size_t)j * ldv, i);
+        const TV* vj = V + (size_t)j * ldv;
         double2 c = sc[j * R + r];
         AT cr = (AT)(sign * c.x), ci = (AT)(sign * c.y);
-        acc.re += cr * v.re - ci * v.im;
-        acc.im += cr * v.im + ci * v.re;
+#pragma unroll
+        for (int u = 0; u < EPT; u++) {
+          size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
+          cplx<AT> v = in[u] ? ldc<AT>(vj, i) : cplx<AT>(0, 0);
+          acc[u].re += cr * v.re - ci * v.im;
+          acc[u].im += cr * v.im + ci * v.re;
+        }
       }
-      st2(w, i, acc.re, acc.im);
-      nn += (double)(acc.re * acc.re + acc.im * acc.im);
+#pragma unroll
+      for (int u = 0; u < EPT; u++) {
+        if (!in[u]) continue;
+        size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
+        st2(w, i, acc[u].re, acc[u].im);
+        nn += (double)(acc[u].re * acc[u].re + acc[u].im * acc[u].im);
+      }
     }
     if (npartial) {
       double2 s = rhs_reduce(make_double2(nn, 0), R, red);
@@ -143,18 +165,36 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
   } else {
     TW* wr = w + (size_t)r_sep * n;
     const TV* Vr = V + (size_t)r_sep * n;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)G * blockDim.x) {
-      typedef typename Acc<TV, TW>::T AT;
-      auto acc = ldc<AT>(wr, i);
+    const size_t span = (size_t)blockDim.x * EPT;
+    for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)G * span) {
+      cplx<AT> acc[EPT];
+      bool in[EPT];
+#pragma unroll
+      for (int u = 0; u < EPT; u++) {
+        size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
+        in[u] = i < n;
+        acc[u] = in[u] ? ldc<AT>(wr, i) : cplx<AT>(0, 0);
+      }
+#pragma unroll 2
       for (int j = 0; j < nvec; j++) {
-        auto v = ldc<AT>(Vr + (size_t)j * ldv, i);
+        const TV* vj = Vr + (size_t)j * ldv;
         double2 c = sc[j];
         AT cr = (AT)(sign * c.x), ci = (AT)(sign * c.y);
-        acc.re += cr * v.re - ci * v.im;
-        acc.im += cr * v.im + ci * v.re;
+#pragma unroll
+        for (int u = 0; u < EPT; u++) {
+          size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
+          cplx<AT> v = in[u] ? ldc<AT>(vj, i) : cplx<AT>(0, 0);
+          acc[u].re += cr * v.re - ci * v.im;
+          acc[u].im += cr * v.im + ci * v.re;
+        }
       }
-      st2(wr, i, acc.re, acc.im);
-      nn += (double)(acc.re * acc.re + acc.im * acc.im);
+#pragma unroll
+      for (int u = 0; u < EPT; u++) {
+        if (!in[u]) continue;
+        size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
+        st2(wr, i, acc[u].re, acc[u].im);
+        nn += (double)(acc[u].re * acc[u].re + acc[u].im * acc[u].im);
+      }
     }
     if (npartial) {
       double2 s = cta_reduce(make_double2(nn, 0), reinterpret_cast<double*>(red));
@@ -163,29 +203,35 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
   }
 }
 
-// y(., r) = a[r] x(., r) + b[r] y(., r); zero coefficients skip their operand
+// y(., r) = a[r] x(., r) + b[r] y(., r); zero coefficients skip their operand.
+// Interleaved sets: blockDim and the grid stride are multiples of R, so each
+// thread keeps one right-hand side; separate sets: grid.y = right-hand side.
 template <typename TX, typename TY, bool INTER>
 __global__ void k_baxpby(const double2* __restrict__ a, const TX* x, const double2* __restrict__ b, TY* y, size_t n, int R) {
-  const size_t N = n * R;
+  const int r = INTER ? (int)(threadIdx.x % R) : blockIdx.y;
+  const double2 ca = a[r], cb = b[r];
+  const bool ra = ca.x != 0 || ca.y != 0, rb = cb.x != 0 || cb.y != 0;
+  const size_t N = INTER ? n * R : n;
+  const size_t off = INTER ? 0 : (size_t)r * n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    const int r = INTER ? (int)(i % R) : (int)(i / n);
-    const double2 ca = a[r], cb = b[r];
-    const bool ra = ca.x != 0 || ca.y != 0, rb = cb.x != 0 || cb.y != 0;
-    double2 u = ra ? ld2(x, i) : make_double2(0, 0), v = rb ? ld2(y, i) : make_double2(0, 0);
+    double2 u = ra ? ld2(x, off + i) : make_double2(0, 0), v = rb ? ld2(y, off + i) : make_double2(0, 0);
     double re = ca.x * u.x - ca.y * u.y + cb.x * v.x - cb.y * v.y;
     double im = ca.x * u.y + ca.y * u.x + cb.x * v.y + cb.y * v.x;
-    st2(y, i, re, im);
+    st2(y, off + i, re, im);
   }
 }
 
-// y(., r) = a[r] x(., r)  (x may equal y)
+// y(., r) = a[r] x(., r)  (x may equal y); layout handling as k_baxpby
 template <typename TX, typename TY, bool INTER>
 __global__ void k_bscale(const double2* __restrict__ a, const TX* x, TY* y, size_t n, int R) {
-  const size_t N = n * R;
+  typedef typename Acc<TX, TY>::T AT;
+  const int r = INTER ? (int)(threadIdx.x % R) : blockIdx.y;
+  const AT cr = (AT)a[r].x, ci = (AT)a[r].y;
+  const size_t N = INTER ? n * R : n;
+  const size_t off = INTER ? 0 : (size_t)r * n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    const int r = INTER ? (int)(i % R) : (int)(i / n);
-    const double2 ca = a[r], u = ld2(x, i);
-    st2(y, i, ca.x * u.x - ca.y * u.y, ca.x * u.y + ca.y * u.x);
+    cplx<AT> u = ldc<AT>(x, off + i);
+    st2(y, off + i, cr * u.re - ci * u.im, cr * u.im + ci * u.re);
   }
 }
 
@@ -304,12 +350,17 @@ static void maxpy_launch(dim3 grid, int bd, size_t smem, cudaStream_t st, B* w, 
   k_bmaxpy<A, B, INTER><<<grid, bd, smem, st>>>(w, V, ldv, nvec, dc, n, R, sign, npart);
 }
 
+static int maxpy_grid(size_t work, int bd) {
+  size_t g = (work + (size_t)bd * 4 - 1) / ((size_t)bd * 4);
+  return (int)(g < 1 ? 1 : (g > 16384 ? 16384 : g));
+}
+
 void Blas::maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_host, double sign,
                  double* norms2_host) {
   ScopedTimer timer_("blas_maxpy", st);
   const int R = w.R;
   int bd = w.inter ? inter_block(R) : 256;
-  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  int G = maxpy_grid(w.inter ? w.n * R : w.n, bd);
   const double2* dc = coef_to_device(this, coef_host, (size_t)nvec * R, "blas_coef");
   double2* npart = norms2_host ? (double2*)pool->get("blas_npartial", (size_t)R * G * sizeof(double2)) : nullptr;
   size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
@@ -333,19 +384,34 @@ void Blas::maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const doubl
   }
 }
 
+static void elementwise_grid(const VSet& y, int* bd, dim3* grid) {
+  if (y.inter) {
+    *bd = inter_block(y.R);
+    size_t g = (y.n * y.R + *bd - 1) / *bd;
+    grid->x = (unsigned)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+    grid->y = 1;
+  } else {
+    *bd = 256;
+    size_t g = (y.n + 255) / 256;
+    grid->x = (unsigned)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+    grid->y = y.R;
+  }
+  grid->z = 1;
+}
+
 void Blas::axpby(const double2* a_host, const VSet& x, const double2* b_host, const VSet& y) {
   ScopedTimer timer_("blas_axpby", st);
   const int R = y.R;
   std::vector<double2> ab(2 * (size_t)R);
   for (int r = 0; r < R; r++) { ab[r] = a_host[r]; ab[R + r] = b_host[r]; }
   const double2* d = coef_to_device(this, ab.data(), 2 * (size_t)R, "blas_ab");
-  size_t N = y.n * R;
-  size_t g = (N + 255) / 256;
-  unsigned grid = (unsigned)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+  int bd;
+  dim3 grid;
+  elementwise_grid(y, &bd, &grid);
   if (y.inter)
-    DISPATCH_TYPES(x.type, y.type, (k_baxpby<A, B, true><<<grid, 256, 0, st>>>(d, (const A*)x.p, d + R, (B*)y.p, y.n, R)));
+    DISPATCH_TYPES(x.type, y.type, (k_baxpby<A, B, true><<<grid, bd, 0, st>>>(d, (const A*)x.p, d + R, (B*)y.p, y.n, R)));
   else
-    DISPATCH_TYPES(x.type, y.type, (k_baxpby<A, B, false><<<grid, 256, 0, st>>>(d, (const A*)x.p, d + R, (B*)y.p, y.n, R)));
+    DISPATCH_TYPES(x.type, y.type, (k_baxpby<A, B, false><<<grid, bd, 0, st>>>(d, (const A*)x.p, d + R, (B*)y.p, y.n, R)));
   CKL("baxpby");
 }
 
@@ -374,7 +440,7 @@ void Blas::maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const d
   ScopedTimer timer_("blas_maxpy", st);
   const int R = w.R;
   int bd = w.inter ? inter_block(R) : 256;
-  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  int G = maxpy_grid(w.inter ? w.n * R : w.n, bd);
   double2* npart = norms2_dev ? (double2*)pool->get("blas_npartial_dev", (size_t)R * G * sizeof(double2)) : nullptr;
   size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
   if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");
@@ -393,15 +459,15 @@ void Blas::maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const d
 }
 
 void Blas::scale_dev(const double2* a_dev, const VSet& x, const VSet& y) {
-  ScopedTimer timer_("blas_axpby", st);
+  ScopedTimer timer_("blas_scale", st);
   const int R = y.R;
-  size_t N = y.n * R;
-  size_t gsz = (N + 255) / 256;
-  unsigned grid = (unsigned)(gsz < 1 ? 1 : (gsz > 8192 ? 8192 : gsz));
+  int bd;
+  dim3 grid;
+  elementwise_grid(y, &bd, &grid);
   if (y.inter)
-    DISPATCH_TYPES(x.type, y.type, (k_bscale<A, B, true><<<grid, 256, 0, st>>>(a_dev, (const A*)x.p, (B*)y.p, y.n, R)));
+    DISPATCH_TYPES(x.type, y.type, (k_bscale<A, B, true><<<grid, bd, 0, st>>>(a_dev, (const A*)x.p, (B*)y.p, y.n, R)));
   else
-    DISPATCH_TYPES(x.type, y.type, (k_bscale<A, B, false><<<grid, 256, 0, st>>>(a_dev, (const A*)x.p, (B*)y.p, y.n, R)));
+    DISPATCH_TYPES(x.type, y.type, (k_bscale<A, B, false><<<grid, bd, 0, st>>>(a_dev, (const A*)x.p, (B*)y.p, y.n, R)));
   CKL("bscale");
 }
 
@@ -429,8 +495,15 @@ __global__ void k_arnoldi_start(ArnoldiDev a, const double2* __restrict__ nr2) {
   a.scale[r] = make_double2(beta > 0 ? 1.0 / beta : 0.0, 0);
 }
 
+template <typename T>
 __global__ void k_arnoldi_step(ArnoldiDev a, int j, const double2* __restrict__ h, const double2* __restrict__ h2,
                                const double2* __restrict__ hn2) {
+  // one thread per system; its Hessenberg column (j + 2 entries) is kept in
+  // shared memory so the sequential rotations do not wait on global loads;
+  // T = float for loose tolerances (the rotations are a long dependent chain,
+  // and FP64 latency is high on this GPU), double otherwise
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* col = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)threadIdx.x * (j + 2);
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.R) return;
   const int m = a.m, R = a.R;
@@ -438,24 +511,27 @@ __global__ void k_arnoldi_step(ArnoldiDev a, int j, const double2* __restrict__ 
   for (int i = 0; i <= j; i++) {
     double2 v = h[(size_t)i * R + r];
     if (h2) { v.x += h2[(size_t)i * R + r].x; v.y += h2[(size_t)i * R + r].y; }
-    H[(size_t)i * m + j] = v;
+    col[i] = cplx<T>((T)v.x, (T)v.y);
   }
   double hn = sqrt(hn2[r].x);
-  H[(size_t)(j + 1) * m + j] = make_double2(hn, 0);
+  col[j + 1] = cplx<T>((T)hn, 0);
+  const double2* csr = a.cs + (size_t)r * m;
+  const double2* snr = a.sn + (size_t)r * m;
   for (int i = 0; i < j; i++) {
-    cplx<double> x = zc2(H[(size_t)i * m + j]), y = zc2(H[(size_t)(i + 1) * m + j]);
-    cplx<double> c = zc2(a.cs[(size_t)r * m + i]), s = zc2(a.sn[(size_t)r * m + i]);
-    H[(size_t)i * m + j] = zd2(conj(c) * x + conj(s) * y);
-    H[(size_t)(i + 1) * m + j] = zd2(c * y - s * x);
+    cplx<T> c((T)csr[i].x, (T)csr[i].y), s((T)snr[i].x, (T)snr[i].y);
+    cplx<T> x = col[i], y = col[i + 1];
+    col[i] = conj(c) * x + conj(s) * y;
+    col[i + 1] = c * y - s * x;
   }
-  cplx<double> d = zc2(H[(size_t)j * m + j]);
+  cplx<double> d((double)col[j].re, (double)col[j].im);
   double rho = sqrt(norm2(d) + hn * hn);
   cplx<double> c = rho > 0 ? cplx<double>(d.re / rho, d.im / rho) : cplx<double>(1, 0);
   cplx<double> s = rho > 0 ? cplx<double>(hn / rho, 0) : cplx<double>(0, 0);
   a.cs[(size_t)r * m + j] = zd2(c);
   a.sn[(size_t)r * m + j] = zd2(s);
-  H[(size_t)j * m + j] = make_double2(rho, 0);
-  H[(size_t)(j + 1) * m + j] = make_double2(0, 0);
+  col[j] = cplx<T>((T)rho, 0);
+  col[j + 1] = cplx<T>(0, 0);
+  for (int i = 0; i <= j + 1; i++) H[(size_t)i * m + j] = make_double2((double)col[i].re, (double)col[i].im);
   double2* g = a.g + (size_t)r * (m + 1);
   cplx<double> gj = zc2(g[j]);
   g[j + 1] = zd2(-(s * gj));
@@ -486,11 +562,29 @@ void launch_arnoldi_start(const ArnoldiDev& a, const double2* nr2, cudaStream_t 
   CKL("arnoldi_start");
 }
 void launch_arnoldi_step(const ArnoldiDev& a, int j, const double2* h, const double2* h2, const double2* hn2,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool fp32) {
   ScopedTimer timer_("arnoldi", st);
-  k_arnoldi_step<<<(a.R + 63) / 64, 64, 0, st>>>(a, j, h, h2, hn2);
+  const int threads = a.R < 32 ? a.R : 32;  // at most 32 x (250 + 2) x 16 B of shared memory
+  if (fp32) {
+    size_t smem = (size_t)threads * (j + 2) * sizeof(cplx<float>);
+    static bool cfg = false;
+    if (!cfg) {
+      CK(cudaFuncSetAttribute(k_arnoldi_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      cfg = true;
+    }
+    k_arnoldi_step<float><<<(a.R + threads - 1) / threads, threads, smem, st>>>(a, j, h, h2, hn2);
+  } else {
+    size_t smem = (size_t)threads * (j + 2) * sizeof(cplx<double>);
+    static bool cfg = false;
+    if (!cfg) {
+      CK(cudaFuncSetAttribute(k_arnoldi_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      cfg = true;
+    }
+    k_arnoldi_step<double><<<(a.R + threads - 1) / threads, threads, smem, st>>>(a, j, h, h2, hn2);
+  }
   CKL("arnoldi_step");
 }
+
 void launch_arnoldi_solve(const ArnoldiDev& a, int k, double2* y, cudaStream_t st) {
   k_arnoldi_solve<<<(a.R + 63) / 64, 64, 0, st>>>(a, k, y);
   CKL("arnoldi_solve");

@@ -67,8 +67,9 @@ struct ArnoldiDev {
 void launch_arnoldi_start(const ArnoldiDev& a, const double2* nr2, cudaStream_t st);
 // column j from the Gram-Schmidt coefficients h (+ h2 if non-null), [i*R + r],
 // and the squared norm of the orthogonalised vector hn2[r].x
+// fp32: rotations in FP32 arithmetic (state kept in FP64), for loose tolerances
 void launch_arnoldi_step(const ArnoldiDev& a, int j, const double2* h, const double2* h2, const double2* hn2,
-                         cudaStream_t st);
+                         cudaStream_t st, bool fp32);
 // y[i*R + r] from the triangular systems of the first k columns
 void launch_arnoldi_solve(const ArnoldiDev& a, int k, double2* y, cudaStream_t st);
 

@@ -177,50 +177,82 @@ __device__ __forceinline__ void load_rc(const cplx<float>* p, cplx<float> v[RC])
   }
 }
 
+// Two consecutive rows (r, r+1) of column k of a column-major block: one
+// 16-byte (FP32) or 8-byte (FP16) load.
+template <typename DS> __device__ __forceinline__ void ld_rows2(const DS* p, cplx<float>& a0, cplx<float>& a1);
+template <> __device__ __forceinline__ void ld_rows2<float2>(const float2* p, cplx<float>& a0, cplx<float>& a1) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a0 = cplx<float>(v.x, v.y);
+  a1 = cplx<float>(v.z, v.w);
+}
+template <> __device__ __forceinline__ void ld_rows2<__half2>(const __half2* p, cplx<float>& a0, cplx<float>& a1) {
+  float2 raw = __ldg(reinterpret_cast<const float2*>(p));
+  __half2 h0 = *reinterpret_cast<__half2*>(&raw.x), h1 = *reinterpret_cast<__half2*>(&raw.y);
+  float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+  a0 = cplx<float>(f0.x, f0.y);
+  a1 = cplx<float>(f1.x, f1.y);
+}
+
+// acc{0,1}[c] += A[r0 + {0,1}][k] v[k][c] for a column-major n x n block whose
+// row r0 is at A; the column loop is unrolled so that many independent
+// matrix loads are in flight per thread.
 template <typename DS, int RC>
-__device__ __forceinline__ void block_mv(const DS* A, const cplx<float>* v, int n, int R, cplx<float> acc[RC]) {
-#pragma unroll 4
+__device__ __forceinline__ void block_mv2(const DS* A, const cplx<float>* v, int n, int R, cplx<float> acc0[RC],
+                                          cplx<float> acc1[RC]) {
+#pragma unroll 8
   for (int k = 0; k < n; k++) {
-    cplx<float> a = ldD<DS>(A + (size_t)k * n);
+    cplx<float> a0, a1;
+    ld_rows2<DS>(A + (size_t)k * n, a0, a1);
     cplx<float> x[RC];
     load_rc<RC>(v + (size_t)k * R, x);
 #pragma unroll
-    for (int c = 0; c < RC; c++) cmac(acc[c], a, x[c]);
+    for (int c = 0; c < RC; c++) {
+      cmac(acc0[c], a0, x[c]);
+      cmac(acc1[c], a1, x[c]);
+    }
   }
 }
 
+// Threads of a site: n/2 row pairs x (R / RC) right-hand-side chunks, row pair
+// fastest (a warp reads consecutive 16-byte pieces of a column); SPB sites per CTA.
 template <typename DS, int RC>
-__global__ void k_coarse_apply(cplx<float>* __restrict__ y, const cplx<float>* __restrict__ x_self,
-                               const cplx<float>* __restrict__ x_hop, const DS* __restrict__ Dc, const int* __restrict__ tab,
-                               const int* __restrict__ osite, int nout, int n, int nv, int R, float mu_c, int mode,
-                               float sres, float sy) {
-  const int nch = R / RC, per = n * nch, spb = blockDim.x / per;
-  const int t = threadIdx.x, r = t % n, ch = (t / n) % nch, q = t / per;
+__global__ void __launch_bounds__(256) k_coarse_apply(cplx<float>* __restrict__ y, const cplx<float>* __restrict__ x_self,
+                                                       const cplx<float>* __restrict__ x_hop, const DS* __restrict__ Dc,
+                                                       const int* __restrict__ tab, const int* __restrict__ osite, int nout,
+                                                       int n, int nv, int R, float mu_c, int mode, float sres, float sy) {
+  const int np = n / 2, nch = R / RC, per = np * nch, spb = blockDim.x / per;
+  const int t = threadIdx.x, rp = t % np, ch = (t / np) % nch, q = t / per;
   const int idx = blockIdx.x * spb + q;
   if (q >= spb || idx >= nout) return;
   const int site = osite ? osite[idx] : idx;
-  const int c0 = ch * RC;
-  cplx<float> acc[RC];
+  const int r0 = 2 * rp, c0 = ch * RC;
+  cplx<float> acc0[RC], acc1[RC];
 #pragma unroll
-  for (int c = 0; c < RC; c++) acc[c] = cplx<float>(0, 0);
+  for (int c = 0; c < RC; c++) acc0[c] = acc1[c] = cplx<float>(0, 0);
   if (mode & 1) {
-    block_mv<DS, RC>(Dc + (size_t)site * 9 * n * n + r, x_self + (size_t)idx * n * R + c0, n, R, acc);
-    float m = r < nv ? mu_c : -mu_c;
-    cplx<float> xv[RC];
-    load_rc<RC>(x_self + ((size_t)idx * n + r) * R + c0, xv);
+    block_mv2<DS, RC>(Dc + (size_t)site * 9 * n * n + r0, x_self + (size_t)idx * n * R + c0, n, R, acc0, acc1);
+    cplx<float> xv0[RC], xv1[RC];
+    load_rc<RC>(x_self + ((size_t)idx * n + r0) * R + c0, xv0);
+    load_rc<RC>(x_self + ((size_t)idx * n + r0 + 1) * R + c0, xv1);
+    const float m0 = r0 < nv ? mu_c : -mu_c, m1 = r0 + 1 < nv ? mu_c : -mu_c;
 #pragma unroll
-    for (int c = 0; c < RC; c++) acc[c] = acc[c] + m * times_i(xv[c]);
+    for (int c = 0; c < RC; c++) {
+      acc0[c] = acc0[c] + m0 * times_i(xv0[c]);
+      acc1[c] = acc1[c] + m1 * times_i(xv1[c]);
+    }
   }
   if (mode & 2)
     for (int d = 1; d < 9; d++) {
       const int src = __ldg(tab + (size_t)(d - 1) * nout + idx);
-      block_mv<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r, x_hop + (size_t)src * n * R + c0, n, R, acc);
+      block_mv2<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r0, x_hop + (size_t)src * n * R + c0, n, R, acc0, acc1);
     }
-  cplx<float>* yo = y + ((size_t)idx * n + r) * R + c0;
+  cplx<float>* yo0 = y + ((size_t)idx * n + r0) * R + c0;
+  cplx<float>* yo1 = yo0 + R;
 #pragma unroll
   for (int c = 0; c < RC; c++) {
-    cplx<float> res = sres * acc[c];
-    yo[c] = sy == 0.f ? res : sy * yo[c] + res;
+    cplx<float> res0 = sres * acc0[c], res1 = sres * acc1[c];
+    yo0[c] = sy == 0.f ? res0 : sy * yo0[c] + res0;
+    yo1[c] = sy == 0.f ? res1 : sy * yo1[c] + res1;
   }
 }
 
@@ -229,44 +261,56 @@ __global__ void k_coarse_apply(cplx<float>* __restrict__ y, const cplx<float>* _
 // the hop result of a site goes through shared memory to the threads of the
 // same site for the dense matvec with the inverse.
 template <typename DS, int RC>
-__global__ void k_coarse_even(cplx<float>* __restrict__ t, const cplx<float>* __restrict__ rhs, const cplx<float>* __restrict__ v,
-                              const DS* __restrict__ Dc, const float2* __restrict__ Dinv, const int* __restrict__ tab,
-                              const int* __restrict__ even, int ne, int n, int R, float sr, float sh) {
+__global__ void __launch_bounds__(256) k_coarse_even(cplx<float>* __restrict__ t, const cplx<float>* __restrict__ rhs,
+                                                      const cplx<float>* __restrict__ v, const DS* __restrict__ Dc,
+                                                      const float2* __restrict__ Dinv, const int* __restrict__ tab,
+                                                      const int* __restrict__ even, int ne, int n, int R, float sr, float sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nch = R / RC, per = n * nch, spb = blockDim.x / per;
+  const int np = n / 2, nch = R / RC, per = np * nch, spb = blockDim.x / per;
   cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem_raw);  // [spb][n][R]
-  const int th = threadIdx.x, r = th % n, ch = (th / n) % nch, q = th / per;
+  const int th = threadIdx.x, rp = th % np, ch = (th / np) % nch, q = th / per;
   const int e = blockIdx.x * spb + q;
   const bool act = q < spb && e < ne;
-  const int c0 = ch * RC;
+  const int r0 = 2 * rp, c0 = ch * RC;
   if (act) {
     const int site = even[e];
-    cplx<float> acc[RC];
+    cplx<float> acc0[RC], acc1[RC];
 #pragma unroll
-    for (int c = 0; c < RC; c++) acc[c] = cplx<float>(0, 0);
+    for (int c = 0; c < RC; c++) acc0[c] = acc1[c] = cplx<float>(0, 0);
     if (v)
       for (int d = 1; d < 9; d++) {
         const int src = __ldg(tab + (size_t)(d - 1) * ne + e);
-        block_mv<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r, v + (size_t)src * n * R + c0, n, R, acc);
+        block_mv2<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r0, v + (size_t)src * n * R + c0, n, R, acc0, acc1);
       }
-    cplx<float> rv[RC];
-    if (rhs) load_rc<RC>(rhs + ((size_t)e * n + r) * R + c0, rv);
+    cplx<float> rv0[RC], rv1[RC];
+    if (rhs) {
+      load_rc<RC>(rhs + ((size_t)e * n + r0) * R + c0, rv0);
+      load_rc<RC>(rhs + ((size_t)e * n + r0 + 1) * R + c0, rv1);
+    }
 #pragma unroll
     for (int c = 0; c < RC; c++) {
-      cplx<float> a = sh * acc[c];
-      if (rhs) a = a + sr * rv[c];
-      hs[((size_t)q * n + r) * R + c0 + c] = a;
+      cplx<float> a0 = sh * acc0[c], a1 = sh * acc1[c];
+      if (rhs) {
+        a0 = a0 + sr * rv0[c];
+        a1 = a1 + sr * rv1[c];
+      }
+      hs[((size_t)q * n + r0) * R + c0 + c] = a0;
+      hs[((size_t)q * n + r0 + 1) * R + c0 + c] = a1;
     }
   }
   __syncthreads();
   if (act) {
-    cplx<float> out[RC];
+    cplx<float> o0[RC], o1[RC];
 #pragma unroll
-    for (int c = 0; c < RC; c++) out[c] = cplx<float>(0, 0);
-    block_mv<float2, RC>(Dinv + (size_t)e * n * n + r, hs + (size_t)q * n * R + c0, n, R, out);
-    cplx<float>* to = t + ((size_t)e * n + r) * R + c0;
+    for (int c = 0; c < RC; c++) o0[c] = o1[c] = cplx<float>(0, 0);
+    block_mv2<float2, RC>(Dinv + (size_t)e * n * n + r0, hs + (size_t)q * n * R + c0, n, R, o0, o1);
+    cplx<float>* to0 = t + ((size_t)e * n + r0) * R + c0;
+    cplx<float>* to1 = to0 + R;
 #pragma unroll
-    for (int c = 0; c < RC; c++) to[c] = out[c];
+    for (int c = 0; c < RC; c++) {
+      to0[c] = o0[c];
+      to1[c] = o1[c];
+    }
   }
 }
 
@@ -341,11 +385,12 @@ __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__
 
 // threads per CTA: whole sites of n * (R / RC) threads, at most 256 per CTA
 static int sites_per_cta(int per) { return per >= 256 ? 1 : 256 / per; }
+static int threads_per_site(int n, int R, int RC) { return n / 2 * (R / RC); }
 
 template <typename DS, int RC>
 static void coarse_apply_t(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
                            const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  int per = c.n * (R / RC), spb = sites_per_cta(per);
+  int per = threads_per_site(c.n, R, RC), spb = sites_per_cta(per);
   unsigned grid = (unsigned)((nout + spb - 1) / spb);
   if (grid == 0) return;
   k_coarse_apply<DS, RC><<<grid, spb * per, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, R, (float)mu_c,
@@ -380,7 +425,7 @@ void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<
 template <typename DS, int RC>
 static void coarse_even_t(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
                           float sh, cudaStream_t st) {
-  int per = c.n * (R / RC), spb = sites_per_cta(per);
+  int per = threads_per_site(c.n, R, RC), spb = sites_per_cta(per);
   int ne = (int)c.h_even.size();
   unsigned grid = (unsigned)((ne + spb - 1) / spb);
   if (grid == 0) return;

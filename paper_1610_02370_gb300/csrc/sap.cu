@@ -55,7 +55,7 @@ __device__ __forceinline__ void cta_sum3(R& a, R& b, R& c, R* red) {
 }
 
 template <int P>
-__global__ void k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, SiteInv<P> Ainv, Geo g,
+__global__ void __launch_bounds__(128, 3) k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, SiteInv<P> Ainv, Geo g,
                            SapArgs<typename Prec<P>::real> a) {
   typedef typename Prec<P>::real R;
   typedef cplx<R> Z;
@@ -92,7 +92,7 @@ __global__ void k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, Si
     Z bb[12], dx[12];
     b.load(blk, le, bb);
     if (!a.zero_x) {
-      dslash_site<P>(x, U, C, g, a.mu, blk, le, dx);
+      dslash_site<P, 1>(x, U, C, g, a.mu, blk, le, dx);
 #pragma unroll
       for (int c = 0; c < 12; c++) bb[c] = bb[c] - dx[c];
     }
@@ -104,7 +104,7 @@ __global__ void k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, Si
     for (int c = 0; c < 12; c++) te[c * Vh + i] = t[c];
     b.load(blk, lo, bb);
     if (!a.zero_x) {
-      dslash_site<P>(x, U, C, g, a.mu, blk, lo, dx);
+      dslash_site<P, 1>(x, U, C, g, a.mu, blk, lo, dx);
 #pragma unroll
       for (int c = 0; c < 12; c++) bb[c] = bb[c] - dx[c];
     }

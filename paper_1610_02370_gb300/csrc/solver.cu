@@ -218,7 +218,7 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
         B.dots_dev(vs(V), N, j + 1, vs(w), h2);
         B.maxpy_dev(vs(w), vs(V), N, j + 1, h2, -1.0, nr2);
       }
-      launch_arnoldi_step(ad, j, h, reorth ? h2 : nullptr, nr2, c->stream);
+      launch_arnoldi_step(ad, j, h, reorth ? h2 : nullptr, nr2, c->stream, tol >= 1e-3);
       fetch_est(j & 1);
       if (j < m - 1) B.scale_dev(ad.scale, vs(w), vs(V + (size_t)(j + 1) * N));  // V_{j+1} = w / ||w||
       iters++;
@@ -458,7 +458,7 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
       B.maxpy_dev(s32(w), s32(V), (size_t)R * n, j + 1, h, -1.0, nullptr);
       B.dots_dev(s32(V), (size_t)R * n, j + 1, s32(w), h2);
       B.maxpy_dev(s32(w), s32(V), (size_t)R * n, j + 1, h2, -1.0, nr2);
-      launch_arnoldi_step(ad, j, h, h2, nr2, c->stream);
+      launch_arnoldi_step(ad, j, h, h2, nr2, c->stream, false);
       fetch_est(j & 1);
       if (j < m - 1) B.scale_dev(ad.scale, s32(w), s32(Vj(j + 1)));
       res.iters++;

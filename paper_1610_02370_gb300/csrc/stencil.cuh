@@ -8,8 +8,9 @@
 
 namespace ddtm {
 
-// out = D(mu) x at internal site (blk, loc): clover + twist + 8 hops
-template <int P>
+// out = D(mu) x at internal site (blk, loc): clover + twist + 8 hops.
+// UNROLL = 1 keeps the direction loop rolled (register pressure inside SAP).
+template <int P, int UNROLL = 4>
 __device__ __forceinline__ void dslash_site(const Spinor<P>& x, const Links<P>& U, const Clover<P>& C, const Geo& g,
                                             typename Prec<P>::real mu, int blk, int loc,
                                             cplx<typename Prec<P>::real> out[12]) {
@@ -17,9 +18,9 @@ __device__ __forceinline__ void dslash_site(const Spinor<P>& x, const Links<P>& 
   cplx<R> acc[12];
 #pragma unroll
   for (int c = 0; c < 12; c++) acc[c] = cplx<R>(0, 0);
-#pragma unroll
+#pragma unroll (UNROLL)
   for (int mu_ = 0; mu_ < 4; mu_++) {
-#pragma unroll
+#pragma unroll (UNROLL == 1 ? 1 : 2)
     for (int dir = 0; dir < 2; dir++) {
       bool fwd = dir == 0;
       Nbr n = neighbour(g, blk, loc, 2 * mu_ + dir);
@@ -64,9 +65,9 @@ __device__ __forceinline__ void hop_block(const cplx<R>* v, int Vh, const Links<
   cplx<R> acc[12];
 #pragma unroll
   for (int c = 0; c < 12; c++) acc[c] = cplx<R>(0, 0);
-#pragma unroll
+#pragma unroll 1
   for (int mu_ = 0; mu_ < 4; mu_++) {
-#pragma unroll
+#pragma unroll 1
     for (int dir = 0; dir < 2; dir++) {
       bool fwd = dir == 0;
       uint32_t e = __ldg(g.loc_nbr + (2 * mu_ + dir) * g.Vb + loc);
