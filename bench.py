@@ -47,7 +47,7 @@ WORKLOADS = {
 # the paper does per ensemble: at 24^3x48 one setup then single-rhs solves gave 4 cycles: no convergence
 # in 120 iterations; 2 cycles: 22 iterations; 1 cycle: 27 (parameter study recorded with the design notes).
 MG = dict(block=(4, 4, 4, 4), nv=24, n_setup=6, post_smooth=2, nmr=3, outer_restart=30, outer_tol=1e-10,
-          smoother_prec=2, coarse_prec=1)
+          smoother_prec=2, coarse_prec=2)
 NRHS = 12
 SEED = 2024
 
@@ -84,10 +84,28 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc):
         # 8 hop blocks and the FP32 self-block inverse per even site, read once per batch of NRHS
         d = S2[prec]
         return Nc / 2 * (8 * n * n * d + n * n * 8 + 2 * n * NRHS * 8)
+    if name.startswith("coarse_tc_") or name == "coarse_image":
+        # tensor-core passes on FP16 images: a 2n x n real matrix image per block (16 kpad
+        # bytes per row), a (2 NRHS) x n vector image per site; FP32 vectors n NRHS x 8 bytes
+        kpad = (n + 15) // 16 * 16
+        a_img = 2 * n * kpad * 2
+        v_img = (2 * NRHS + 7) // 8 * 8 * kpad * 2
+        v32 = n * NRHS * 8
+        half = Nc / 2
+        if name == "coarse_tc_hop_even":    # 8 hop blocks per even site, odd input image, even output image
+            return half * (8 * a_img + 2 * v_img)
+        if name == "coarse_tc_inverse":     # inverse block per even site, input and output images
+            return half * (a_img + 2 * v_img)
+        if name == "coarse_tc_odd":         # 9 blocks per odd site, two input images, FP32 twist input and output
+            return half * (9 * a_img + 2 * v_img + 2 * v32)
+        if name == "coarse_tc_full":
+            return Nc * (9 * a_img + v_img + 2 * v32)
+        if name == "coarse_image":          # FP32 odd vector in, image out
+            return half * (v32 + v_img)
     if name.startswith("coarse_apply_odd_"):
-        # launches alternate the self block (1 block) and the 8 hop blocks: 4.5 blocks per odd site on average
+        # self block and 8 hop blocks per odd site; x_o, the even input and y_o
         d = S2[prec]
-        return Nc / 2 * (4.5 * n * n * d + 3 * n * NRHS * 8)
+        return Nc / 2 * (9 * n * n * d + 3 * n * NRHS * 8)
     return None
 
 
@@ -396,8 +414,12 @@ def main():
                 "frac": achieved / hbm if achieved else None, "traffic": None,
                 "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches / args.steps,
                 "bytes_per_launch": nbytes, "peak_source": peak_note}
-    breakdown = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                     "share": v["ms"] / total_ms} for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"])}
+    breakdown = {}
+    for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"]):
+        nb = algorithmic_bytes(k, V, Vb, MG["block"], MG["nv"], Nc)
+        breakdown[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                        "share": v["ms"] / total_ms,
+                        "gbs": nb / (v["ms"] / v["launches"] / 1000.0) / 1e9 if nb else None}
     gpu_launches = int(sum(v["launches"] for v in counts.values()))
 
     # end to end through host buffers: gauge upload + setup + solve with pinned host b and x

@@ -2,13 +2,15 @@
 // build, stencil, even-odd reduction pieces, and the self-block inverses of
 // the even-odd coarsest solve (Sec. 2.5).
 //
-// Storage: Dc[((x*9 + d)*n + col)*n + row], complex FP32 or FP16, n = 2 nv,
+// Storage: Dc[((x*9 + d)*n + col)*n + row], complex FP32, n = 2 nv,
 // d = 0 self (without the twist), d = 1 + k for hop k = 2 mu + (0 fwd, 1 bwd):
 // the block coupling site x to its neighbour in direction +mu (k even) or
 // -mu (k odd).  Column-major blocks make the per-row threads of the stencil
 // read consecutive addresses.  The twist i mu_c Gamma5_c (Gamma5_c = +1 on
 // dofs < nv, -1 above) is added on the fly, so one build serves +mu, -mu and
-// the shifted coarsest twist delta*mu.
+// the shifted coarsest twist delta*mu.  With FP16 coarse storage the stencil
+// of the coarsest solve runs on tensor cores from FP16 images of these blocks
+// (coarse_tc.cu); the FP32 blocks stay for the rest.
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "timer.h"
@@ -124,13 +126,9 @@ void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* D
   int threads = g.Vb >= 256 ? 256 : ((g.Vb + 31) / 32) * 32;
   Links<PREC_F32> U{(const float2*)links32, g.Vb};
   Clover<PREC_F32> C{(const float2*)clover32, g.Vb};
-  if (dprec == PREC_F16) {
-    CK(cudaFuncSetAttribute(k_galerkin<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_galerkin<__half2><<<g.Nb, threads, smem, st>>>((__half2*)Dc, P, U, C, q, f, nv);
-  } else {
-    CK(cudaFuncSetAttribute(k_galerkin<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_galerkin<float2><<<g.Nb, threads, smem, st>>>((float2*)Dc, P, U, C, q, f, nv);
-  }
+  if (dprec != PREC_F32) throw Error(DDTM_ERR_ARG, "internal: Galerkin output is FP32");
+  CK(cudaFuncSetAttribute(k_galerkin<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_galerkin<float2><<<g.Nb, threads, smem, st>>>((float2*)Dc, P, U, C, q, f, nv);
   CKL("galerkin");
 }
 
@@ -326,6 +324,20 @@ __global__ void k_parity_copy(cplx<float>* __restrict__ compact, cplx<float>* __
   else full[f] = compact[t];
 }
 
+// canonical FP64 coarse vector c[site * n + k] <-> column r of an interleaved
+// FP32 batch v[(site * n + k) * R + r] (dir 0: c -> v, dir 1: v -> c)
+__global__ void k_coarse_interleave(float2* __restrict__ v, double* __restrict__ c, size_t nc, int r, int R, int dir) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  if (dir == 0) {
+    v[t * R + r] = make_float2((float)c[2 * t], (float)c[2 * t + 1]);
+  } else {
+    float2 z = v[t * R + r];
+    c[2 * t] = z.x;
+    c[2 * t + 1] = z.y;
+  }
+}
+
 // Inverse of (self block + i mu_c Gamma5_c) per even site by Gauss-Jordan
 // elimination with partial pivoting in FP64; one CTA per site, thread = row.
 template <typename DS>
@@ -408,18 +420,14 @@ static void coarse_apply_d(const CoarseLevel& c, cplx<float>* y, const cplx<floa
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,
                               float sres, float sy, cudaStream_t st) {
   ScopedTimer timer_("coarse_apply", st);
-  if (c.prec == PREC_F16) coarse_apply_d<__half2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, mu_c, mode, sres, sy, st);
-  else coarse_apply_d<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, mu_c, mode, sres, sy, st);
+  coarse_apply_d<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, mu_c, mode, sres, sy, st);
 }
 
 void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e, int R,
                              double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_apply_odd_f16" : "coarse_apply_odd_f32", st);
+  ScopedTimer timer_("coarse_apply_odd_f32", st);
   int no = (int)c.h_odd.size();
-  if (c.prec == PREC_F16)
-    coarse_apply_d<__half2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, R, mu_c, mode, sres, sy, st);
-  else
-    coarse_apply_d<float2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, R, mu_c, mode, sres, sy, st);
+  coarse_apply_d<float2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, R, mu_c, mode, sres, sy, st);
 }
 
 template <typename DS, int RC>
@@ -442,14 +450,9 @@ static void coarse_even_t(const CoarseLevel& c, cplx<float>* t, const cplx<float
 
 void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
                         float sh, cudaStream_t st) {
-  ScopedTimer timer_(c.prec == PREC_F16 ? "coarse_even_f16" : "coarse_even_f32", st);
-  if (c.prec == PREC_F16) {
-    if (R % 4 == 0) coarse_even_t<__half2, 4>(c, t, rhs, v, R, sr, sh, st);
-    else coarse_even_t<__half2, 1>(c, t, rhs, v, R, sr, sh, st);
-  } else {
-    if (R % 4 == 0) coarse_even_t<float2, 4>(c, t, rhs, v, R, sr, sh, st);
-    else coarse_even_t<float2, 1>(c, t, rhs, v, R, sr, sh, st);
-  }
+  ScopedTimer timer_("coarse_even_f32", st);
+  if (R % 4 == 0) coarse_even_t<float2, 4>(c, t, rhs, v, R, sr, sh, st);
+  else coarse_even_t<float2, 1>(c, t, rhs, v, R, sr, sh, st);
 }
 
 void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int R, int dir,
@@ -462,20 +465,23 @@ void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, 
   CKL("parity_copy");
 }
 
+void launch_coarse_interleave(const CoarseLevel& c, cplx<float>* v, double* canon, int r, int R, int dir,
+                              cudaStream_t st) {
+  size_t nc = (size_t)c.Nc * c.n;
+  k_coarse_interleave<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(reinterpret_cast<float2*>(v), canon, nc, r, R, dir);
+  CKL("coarse_interleave");
+}
+
 void launch_self_inverse(CoarseLevel& c, double mu_c, cudaStream_t st) {
   ScopedTimer timer_("self_inverse", st);
   int ne = (int)c.h_even.size();
   c.Dinv.ensure((size_t)ne * c.n * c.n * sizeof(float2));
   size_t smem = (size_t)c.n * 2 * c.n * sizeof(cplx<double>);
   int threads = ((c.n + 31) / 32) * 32;
-  if (c.prec == PREC_F16) {
-    CK(cudaFuncSetAttribute(k_self_inverse<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_self_inverse<__half2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<__half2>(), c.even.as<int>(), c.n, c.nv, mu_c);
-  } else {
-    CK(cudaFuncSetAttribute(k_self_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_self_inverse<float2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(), c.n, c.nv, mu_c);
-  }
+  CK(cudaFuncSetAttribute(k_self_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_self_inverse<float2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(), c.n, c.nv, mu_c);
   CKL("self_inverse");
+  if (c.prec == PREC_F16) build_inverse_images(c, st);
   c.inv_mu = mu_c;
   c.inv_valid = true;
 }

@@ -37,5 +37,48 @@ void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>*
 void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int R, int dir,
                         cudaStream_t st);
 void launch_self_inverse(CoarseLevel& c, double mu_c, cudaStream_t st);
+// canonical FP64 coarse vector <-> column r of an interleaved FP32 batch of R (dir 0: in, 1: out)
+void launch_coarse_interleave(const CoarseLevel& c, cplx<float>* v, double* canon, int r, int R, int dir,
+                              cudaStream_t st);
+
+// coarse_tc.cu: the stencil on tensor cores, FP16 operands and FP32 accumulation.
+// Operands are "images": FP16 copies laid out as the MMA reads them from shared
+// memory (matrix images of the n x n blocks, vector images of R right-hand
+// sides per site); see coarse_tc.cu.
+struct TcGeom {
+  int n, R, kpad, sbo, arows, a_bytes, ngj, b_bytes;
+};
+TcGeom tc_geom(int n, int R);
+bool tc_supported(int n);
+// Dct: matrix images of the 9 blocks of every site (from Dc); Dinvt: of Dinv
+void build_coarse_images(CoarseLevel& c, cudaStream_t st);
+void build_inverse_images(CoarseLevel& c, cudaStream_t st);
+size_t tc_vector_image_bytes(const CoarseLevel& c, int nsites, int R);
+void launch_vector_image(const CoarseLevel& c, void* img, const cplx<float>* x, int nsites, int R, cudaStream_t st);
+// One stencil pass over output slots idx < nout:
+//   acc = [self] A_self(idx) X_self(idx) + [hops] sum_d A_d(site) X_hop(tab[d-1][idx])
+//   y  = sy * yin + sres * (acc + i mu_c Gamma5_c xs)   (FP32, if y)
+//   yt = FP16 vector image of the same value            (if yt)
+struct TcPass {
+  const char* name;
+  bool self = false, hops = false;
+  const void* A_self = nullptr;
+  size_t a_self_stride = 0;
+  bool self_by_site = false;  // A_self indexed by osite[idx] (else by idx)
+  const void* A_hop = nullptr;
+  const void* X_self = nullptr;
+  const void* X_hop = nullptr;
+  const int* tab = nullptr;
+  const int* osite = nullptr;
+  int nout = 0;
+  cplx<float>* y = nullptr;
+  const cplx<float>* yin = nullptr;
+  const cplx<float>* xs = nullptr;
+  float sy = 0.f, sres = 1.f, mu_c = 0.f;
+  void* yt = nullptr;
+};
+void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t st);
+// throws DDTM_ERR_TIMEOUT if a tensor-core pass gave up waiting (and clears the flag)
+void check_tc_error(CoarseLevel& c);
 
 }  // namespace ddtm

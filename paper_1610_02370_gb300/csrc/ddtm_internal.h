@@ -63,9 +63,11 @@ struct CoarseLevel {
   // of odd site i, and [8][Ne] odd-list index of the neighbour of even site i
   std::vector<int> h_nbr_oe, h_nbr_eo;
   DevBuf nbr, even, odd, nbr_oe, nbr_eo;  // device copies
-  int prec = 1;                // storage precision of the operator blocks
-  DevBuf Dc;                   // [site][9][col][row] complex, see coarse.cu
-  DevBuf Dinv;                 // inverses of (self + i mu_c Gamma5_c) on even sites
+  int prec = 1;                // F32: SIMT stencil; F16: tensor-core stencil on FP16 images
+  DevBuf Dc;                   // [site][9][col][row] complex FP32, see coarse.cu
+  DevBuf Dinv;                 // inverses of (self + i mu_c Gamma5_c) on even sites, FP32
+  DevBuf Dct, Dinvt;           // FP16 matrix images of Dc and Dinv (prec F16), see coarse_tc.cu
+  DevBuf tc_err;               // set by a tensor-core pass that gave up waiting
   double inv_mu = 0;
   bool inv_valid = false;
   bool built = false;

@@ -38,6 +38,8 @@ void validate_params(ddtm_ctx* c, const ddtm_params& p) {
     throw Error(DDTM_ERR_ARG, "smoother_prec must be F32 or F16");
   if (p.coarse_prec != DDTM_PREC_F32 && p.coarse_prec != DDTM_PREC_F16)
     throw Error(DDTM_ERR_ARG, "coarse_prec must be F32 or F16");
+  if (p.coarse_prec == DDTM_PREC_F16 && p.nv[0] > 32)
+    throw Error(DDTM_ERR_ARG, "coarse_prec F16 (tensor-core coarse stencil) needs nv[0] <= 32");
 }
 
 void invalidate_setup(ddtm_ctx* c) {
@@ -101,9 +103,10 @@ void build_hierarchy(ddtm_ctx* c) {
   L.nv = nv;
   L.n = 2 * nv;
   L.prec = c->p.coarse_prec;
-  L.Dc.ensure((size_t)L.Nc * 9 * L.n * L.n * (L.prec == PREC_F16 ? 4 : 8));
-  launch_galerkin(g, c->faces, L.prec, L.Dc.p, c->P0.as<float2>(), c->links[PREC_F32].p, c->clover[PREC_F32].p, nv,
+  L.Dc.ensure((size_t)L.Nc * 9 * L.n * L.n * 8);
+  launch_galerkin(g, c->faces, PREC_F32, L.Dc.p, c->P0.as<float2>(), c->links[PREC_F32].p, c->clover[PREC_F32].p, nv,
                   c->stream);
+  if (L.prec == PREC_F16) build_coarse_images(L, c->stream);
   L.inv_valid = false;
   L.built = true;
   c->have_P = true;
@@ -268,11 +271,60 @@ int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full,
   launch_parity_copy(L, 1, bo, (cplx<float>*)b_full, Rc, 0, c->stream);
   launch_coarse_even(L, te, be, nullptr, Rc, 1.f, 0.f, c->stream);                 // te = D_ee^-1 eta_e
   launch_coarse_apply_odd(L, bo, nullptr, te, Rc, mu_c, 2, -1.f, 1.f, c->stream);   // rhat = eta_o - D_oe te
-  OpF32 Dhat = [&](cplx<float>* out, const cplx<float>* in) {
-    launch_coarse_even(L, tA, nullptr, in, Rc, 0.f, 1.f, c->stream);                 // tA = D_ee^-1 D_eo in
-    launch_coarse_apply_odd(L, out, in, nullptr, Rc, mu_c, 1, 1.f, 0.f, c->stream);  // out = D_oo in
-    launch_coarse_apply_odd(L, out, nullptr, tA, Rc, mu_c, 2, -1.f, 1.f, c->stream); // out -= D_oe tA
-  };
+  OpF32 Dhat;
+  if (L.prec == PREC_F16) {
+    // tensor cores: FP16 images of the operand vectors, FP32 accumulation;
+    // only the input and the output of D_hat are FP32 vectors
+    const size_t img_o = tc_vector_image_bytes(L, (int)no, Rc), img_e = tc_vector_image_bytes(L, (int)ne, Rc);
+    char* vt = (char*)c->scratch.get("ceo_vt", img_o);
+    char* ht = (char*)c->scratch.get("ceo_ht", img_e);
+    char* tt = (char*)c->scratch.get("ceo_tt", img_e);
+    const size_t ab = tc_geom(L.n, 1).a_bytes;
+    Dhat = [&, vt, ht, tt, ab](cplx<float>* out, const cplx<float>* in) {
+      launch_vector_image(L, vt, in, (int)no, Rc, c->stream);
+      TcPass h;  // ht = D_eo in
+      h.name = "coarse_tc_hop_even";
+      h.hops = true;
+      h.A_hop = L.Dct.p;
+      h.X_hop = vt;
+      h.tab = L.nbr_eo.as<int>();
+      h.osite = L.even.as<int>();
+      h.nout = (int)ne;
+      h.yt = ht;
+      launch_coarse_tc(L, h, Rc, c->stream);
+      TcPass v;  // tt = -D_ee^-1 ht
+      v.name = "coarse_tc_inverse";
+      v.self = true;
+      v.A_self = L.Dinvt.p;
+      v.a_self_stride = ab;
+      v.X_self = ht;
+      v.nout = (int)ne;
+      v.sres = -1.f;
+      v.yt = tt;
+      launch_coarse_tc(L, v, Rc, c->stream);
+      TcPass o;  // out = (D_oo + i mu_c Gamma5_c) in + D_oe tt
+      o.name = "coarse_tc_odd";
+      o.self = o.hops = true;
+      o.A_self = L.Dct.p;
+      o.a_self_stride = 9 * ab;
+      o.self_by_site = true;
+      o.A_hop = L.Dct.p;
+      o.X_self = vt;
+      o.X_hop = tt;
+      o.tab = L.nbr_oe.as<int>();
+      o.osite = L.odd.as<int>();
+      o.nout = (int)no;
+      o.y = out;
+      o.xs = in;
+      o.mu_c = (float)mu_c;
+      launch_coarse_tc(L, o, Rc, c->stream);
+    };
+  } else {
+    Dhat = [&](cplx<float>* out, const cplx<float>* in) {
+      launch_coarse_even(L, tA, nullptr, in, Rc, 0.f, -1.f, c->stream);               // tA = -D_ee^-1 D_eo in
+      launch_coarse_apply_odd(L, out, in, tA, Rc, mu_c, 3, 1.f, 0.f, c->stream);      // out = D_oo in + D_oe tA
+    };
+  }
   int it = gmres_b(c, Dhat, xo, bo, no * n, Rc, restart, max_restarts, tol, relres, "cgm");
   launch_coarse_even(L, te, be, xo, Rc, 1.f, -1.f, c->stream);  // phi_e = D_ee^-1 (eta_e - D_eo phi_o)
   launch_parity_copy(L, 0, te, x_full, Rc, 1, c->stream);
@@ -618,6 +670,8 @@ int ddtm_setup(ddtm_ctx* ctx, double mu, uint64_t seed) {
   invalidate_setup(ctx);
   double t0 = now_s();
   run_setup(ctx, mu, seed);
+  CK(cudaStreamSynchronize(ctx->stream));
+  check_tc_error(ctx->c1);
   ctx->setup_s = now_s() - t0;
   ctx->setup_done = true;
   ctx->setup_mu = mu;
@@ -717,20 +771,41 @@ int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs
   check_loc(loc);
   if (level != 1 || !x || !y || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments (coarse level is 1)");
   require_hierarchy(ctx);
-  Blas B(ctx->stream, &ctx->scratch);
+  if (nrhs == 0) return DDTM_OK;
   CoarseLevel& L = ctx->c1;
-  size_t nc = (size_t)L.Nc * L.n;
-  cplx<float>* xv = (cplx<float>*)ctx->scratch.get("abi_c32", nc * 8);
-  cplx<float>* yv = (cplx<float>*)ctx->scratch.get("abi_c32b", nc * 8);
+  const size_t nc = (size_t)L.Nc * L.n;
+  // all right-hand sides go through one batched stencil pass
+  cplx<float>* xv = (cplx<float>*)ctx->scratch.get("abi_c32", nc * nrhs * 8);
+  cplx<float>* yv = (cplx<float>*)ctx->scratch.get("abi_c32b", nc * nrhs * 8);
   for (int r = 0; r < nrhs; r++) {
     const double* din = stage_in(ctx, "canon_cin", x + 2 * nc * r, nc, loc);
+    launch_coarse_interleave(L, xv, const_cast<double*>(din), r, nrhs, 0, ctx->stream);
+  }
+  if (L.prec == PREC_F16) {
+    char* xt = (char*)ctx->scratch.get("abi_ct", tc_vector_image_bytes(L, L.Nc, nrhs));
+    launch_vector_image(L, xt, xv, L.Nc, nrhs, ctx->stream);
+    TcPass f;
+    f.name = "coarse_tc_full";
+    f.self = f.hops = true;
+    f.A_self = f.A_hop = L.Dct.p;
+    f.a_self_stride = 9 * (size_t)tc_geom(L.n, 1).a_bytes;
+    f.X_self = f.X_hop = xt;
+    f.tab = L.nbr.as<int>();
+    f.nout = L.Nc;
+    f.y = yv;
+    f.xs = xv;
+    f.mu_c = (float)mu;
+    launch_coarse_tc(L, f, nrhs, ctx->stream);
+  } else {
+    launch_coarse_apply_full(L, yv, xv, nrhs, mu, 3, 1.f, 0.f, ctx->stream);
+  }
+  for (int r = 0; r < nrhs; r++) {
     double* dout = stage_out(ctx, "canon_cout", y + 2 * nc * r, nc, loc);
-    B.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), xv, 1, nc);
-    launch_coarse_apply_full(L, yv, xv, 1, mu, 3, 1.f, 0.f, ctx->stream);
-    B.axpby(make_double2(1, 0), yv, 1, make_double2(0, 0), dout, 0, nc);
+    launch_coarse_interleave(L, yv, dout, r, nrhs, 1, ctx->stream);
     unstage_out(ctx, y + 2 * nc * r, dout, nc, loc);
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  check_tc_error(L);
   API_END(ctx)
 }
 
@@ -752,6 +827,7 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
   B.axpby(make_double2(1, 0), xv, 1, make_double2(0, 0), dout, 0, nc);
   unstage_out(ctx, x, dout, nc, loc);
   CK(cudaStreamSynchronize(ctx->stream));
+  check_tc_error(L);
   if (iters) *iters = it;
   if (rr > ctx->p.coarse_tol) {
     ctx->err = "coarse solve stopped at relative residual " + std::to_string(rr);
@@ -809,6 +885,7 @@ int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, i
     all_conv = all_conv && o.converged;
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  check_tc_error(ctx->c1);
   acc.coarse_iters = ctx->coarse_iters;
   acc.solve_s = now_s() - t0;
   acc.setup_s = ctx->setup_s;
