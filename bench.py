@@ -84,24 +84,6 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc):
         # 8 hop blocks and the FP32 self-block inverse per even site, read once per batch of NRHS
         d = S2[prec]
         return Nc / 2 * (8 * n * n * d + n * n * 8 + 2 * n * NRHS * 8)
-    if name.startswith("coarse_tc_") or name == "coarse_image":
-        # tensor-core passes on FP16 images: a 2n x n real matrix image per block (16 kpad
-        # bytes per row), a (2 NRHS) x n vector image per site; FP32 vectors n NRHS x 8 bytes
-        kpad = (n + 15) // 16 * 16
-        a_img = 2 * n * kpad * 2
-        v_img = (2 * NRHS + 7) // 8 * 8 * kpad * 2
-        v32 = n * NRHS * 8
-        half = Nc / 2
-        if name == "coarse_tc_hop_even":    # 8 hop blocks per even site, odd input image, even output image
-            return half * (8 * a_img + 2 * v_img)
-        if name == "coarse_tc_inverse":     # inverse block per even site, input and output images
-            return half * (a_img + 2 * v_img)
-        if name == "coarse_tc_odd":         # 9 blocks per odd site, two input images, FP32 twist input and output
-            return half * (9 * a_img + 2 * v_img + 2 * v32)
-        if name == "coarse_tc_full":
-            return Nc * (9 * a_img + v_img + 2 * v32)
-        if name == "coarse_image":          # FP32 odd vector in, image out
-            return half * (v32 + v_img)
     if name.startswith("coarse_apply_odd_"):
         # self block and 8 hop blocks per odd site; x_o, the even input and y_o
         d = S2[prec]
@@ -115,7 +97,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="16x16x16x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="32x32x32x64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -228,29 +210,38 @@ def oracle_unit_times(wl, sample_dims=(16, 8, 8, 8)):
 
 
 def oracle_estimate(unit, counts, V, Nc):
-    """Oracle seconds for the GPU step's operation counts (launch counts per kernel)."""
-    def c(prefix):
+    """Oracle seconds for the GPU step's work: every kernel family's work units
+    (right-hand sides or vectors processed, summed over its launches) times the
+    oracle's time for one unit, scaled per site.  Returns (seconds, coarse
+    rhs-iterations)."""
+    def u(prefix):
+        return sum(v.get("units", v["launches"]) for k, v in counts.items() if k.startswith(prefix))
+
+    def n(prefix):
         return sum(v["launches"] for k, v in counts.items() if k.startswith(prefix))
-    solves = c("restrict_")
-    coarse_iters = max(0, c("coarse_even_") - 2 * solves)
+    coarse_iters = u("coarse_tc_hop_even") + u("coarse_tc_full")
+    if coarse_iters == 0:  # FP32 SIMT coarse stencil: one even-site pass per iteration plus two per solve
+        coarse_iters = max(0, u("coarse_even_") - 2 * u("restrict_"))
     t = 0.0
-    t += c("dslash_") * unit["dslash"] * V
-    t += c("sap_half_") * unit["sap_half"] * V
-    t += c("build_P") * unit["build_P"] * V
-    t += c("galerkin") * unit["galerkin"] * V
-    t += solves * unit["restrict"] * V
-    t += c("prolong_") * unit["prolong"] * V
+    t += u("dslash_") * unit["dslash"] * V
+    t += u("sap_half_") * unit["sap_half"] * V
+    t += n("build_P") * unit["build_P"] * V
+    t += n("galerkin") * unit["galerkin"] * V
+    t += u("restrict_") * unit["restrict"] * V
+    t += u("prolong_") * unit["prolong"] * V
     t += coarse_iters * unit["coarse_iter"] * Nc
     return t, coarse_iters
 
 
-# Operation counts of one step of the default workload (kernel launches of
-# the library, from a GPU run of this benchmark), used by the reference arm,
-# which runs no GPU code.  Updated when the method's iteration counts change.
+# Work of one step of the default workload (launches and work units per kernel
+# family of the library, from a GPU run of this benchmark), used by the
+# reference arm, which runs no GPU code.  Updated when the method's iteration
+# counts change.
 REFERENCE_COUNTS = {
-    "dslash_f64": {"launches": 0}, "sap_half_f16": {"launches": 0}, "build_P": {"launches": 6},
-    "galerkin": {"launches": 6}, "restrict_f16": {"launches": 0}, "prolong_f16": {"launches": 0},
-    "coarse_even_f32": {"launches": 0},
+    "dslash_f32": {"launches": 324, "units": 324}, "dslash_f64": {"launches": 24, "units": 24},
+    "sap_half_f16": {"launches": 348, "units": 0}, "build_P": {"launches": 6, "units": 144},
+    "galerkin": {"launches": 6, "units": 6}, "restrict_f16": {"launches": 86, "units": 0},
+    "prolong_f16": {"launches": 86, "units": 0}, "coarse_tc_hop_even": {"launches": 14788, "units": 0},
 }
 
 
@@ -279,7 +270,7 @@ def reference_arm(args):
                        "mg": MG},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "oracle building blocks timed on a %s lattice, scaled per site to %s and "
-                                       "multiplied by the operation counts of one GPU step" % (
+                                       "multiplied by the work units (right-hand sides, vectors) of one GPU step" % (
                                            unit["_sample"], args.workload)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -402,13 +393,21 @@ def main():
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
 
+    # algorithmic bytes per launch: stated by the library for the kernels that
+    # know their operands (coarse passes, Krylov vectors), modelled here otherwise
+    def bytes_per_launch(k):
+        v = counts[k]
+        if v.get("bytes"):
+            return v["bytes"] / v["launches"]
+        return algorithmic_bytes(k, V, Vb, MG["block"], MG["nv"], Nc)
+
     # dominant kernel of the step and its roofline
     kern = sorted(((v["ms"], k) for k, v in counts.items()), reverse=True)
     total_ms = sum(v["ms"] for v in counts.values())
     dom = kern[0][1]
     launches = counts[dom]["launches"]
     avg_s = counts[dom]["ms"] / launches / 1000.0
-    nbytes = algorithmic_bytes(dom, V, Vb, MG["block"], MG["nv"], Nc)
+    nbytes = bytes_per_launch(dom)
     achieved = nbytes / avg_s / 1e9 if nbytes else None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if achieved else None, "traffic": None,
@@ -416,8 +415,9 @@ def main():
                 "bytes_per_launch": nbytes, "peak_source": peak_note}
     breakdown = {}
     for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"]):
-        nb = algorithmic_bytes(k, V, Vb, MG["block"], MG["nv"], Nc)
+        nb = bytes_per_launch(k)
         breakdown[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                        "units_per_step": v.get("units", v["launches"]) / args.steps,
                         "share": v["ms"] / total_ms,
                         "gbs": nb / (v["ms"] / v["launches"] / 1000.0) / 1e9 if nb else None}
     gpu_launches = int(sum(v["launches"] for v in counts.values()))
@@ -448,12 +448,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         unit = oracle_unit_times(wl)
-        per_step_counts = {k: {"launches": v["launches"] / args.steps} for k, v in counts.items()}
+        per_step_counts = {k: {"launches": v["launches"] / args.steps, "units": v.get("units", v["launches"]) / args.steps}
+                           for k, v in counts.items()}
         est, _ = oracle_estimate(unit, per_step_counts, V, Nc)
         cpu = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "oracle building blocks (D, SAP half-sweep, P, Galerkin, R, P, coarse even-odd GMRES "
                          "iteration) timed on a %s lattice with the same couplings and multigrid parameters, scaled "
-                         "per site to %s and multiplied by this step's kernel launch counts" % (
+                         "per site to %s and multiplied by this step's work units (right-hand sides and vectors "
+                         "processed per kernel family)" % (
                              unit["_sample"], args.workload),
                "unit_s_per_site": {k: v for k, v in unit.items() if not k.startswith("_")}}
 
@@ -461,7 +463,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 outer / f32 arithmetic, f16 smoother storage", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 outer; f32 arithmetic; f16 storage (smoother fields, coarse tensor-core "
+                                          "operands)", "data": "synthetic",
             "config": {"workload": "%s twisted-mass clover propagator, 12 point sources, two-level DD-alpha-AMG"
                                    % args.workload, "dims_TXYZ": list(dims), **{k: wl[k] for k in wl if k != "dims"},
                        "mg": MG, "nrhs": NRHS, "l2": "working set (test vectors, P, D_c) far above L2",

@@ -15,17 +15,30 @@ namespace ddtm {
 template <typename T> __device__ __forceinline__ double2 ld2(const T* p, size_t i);
 template <> __device__ __forceinline__ double2 ld2<float2>(const float2* p, size_t i) { float2 a = p[i]; return make_double2(a.x, a.y); }
 template <> __device__ __forceinline__ double2 ld2<double2>(const double2* p, size_t i) { return p[i]; }
+template <> __device__ __forceinline__ double2 ld2<__half2>(const __half2* p, size_t i) { float2 a = __half22float2(p[i]); return make_double2(a.x, a.y); }
 template <typename T> __device__ __forceinline__ void st2(T* p, size_t i, double re, double im);
 template <> __device__ __forceinline__ void st2<float2>(float2* p, size_t i, double re, double im) { p[i] = make_float2((float)re, (float)im); }
 template <> __device__ __forceinline__ void st2<double2>(double2* p, size_t i, double re, double im) { p[i] = make_double2(re, im); }
+template <> __device__ __forceinline__ void st2<__half2>(__half2* p, size_t i, double re, double im) { p[i] = __floats2half2_rn((float)re, (float)im); }
 
 // Arithmetic precision of an operation on two vector types: FP32 when both
-// are FP32 (per-thread partial sums are then short, and every cross-thread
-// reduction is FP64), FP64 otherwise.
+// are FP32 or FP16 (per-thread partial sums are then short, and every
+// cross-thread reduction is FP64), FP64 otherwise.
 template <typename A, typename B> struct Acc { typedef double T; };
 template <> struct Acc<float2, float2> { typedef float T; };
+template <> struct Acc<__half2, float2> { typedef float T; };
+template <> struct Acc<float2, __half2> { typedef float T; };
 template <typename T> __device__ __forceinline__ cplx<T> ldc(const float2* p, size_t i) { float2 a = p[i]; return cplx<T>((T)a.x, (T)a.y); }
 template <typename T> __device__ __forceinline__ cplx<T> ldc(const double2* p, size_t i) { double2 a = p[i]; return cplx<T>((T)a.x, (T)a.y); }
+template <typename T> __device__ __forceinline__ cplx<T> ldc(const __half2* p, size_t i) { float2 a = __half22float2(p[i]); return cplx<T>((T)a.x, (T)a.y); }
+
+// Two consecutive complex entries (i = pair index) as (re0, im0, re1, im1).
+__device__ __forceinline__ float4 ld_pair(const float2* p, size_t i) { return __ldg(reinterpret_cast<const float4*>(p) + i); }
+__device__ __forceinline__ float4 ld_pair(const __half2* p, size_t i) {
+  uint2 u = __ldg(reinterpret_cast<const uint2*>(p) + i);
+  float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x)), b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
 
 // Per-rhs reduction inside a CTA for interleaved sets: thread t holds the
 // partial of right-hand side t % R (blockDim is a multiple of R); thread r < R
@@ -91,6 +104,117 @@ __global__ void k_bdots(const TV* __restrict__ V, size_t ldv, int nvec, const TW
     }
     double2 s = cta_reduce(make_double2(are, aim), reinterpret_cast<double*>(red));
     if (threadIdx.x == 0) partial[(size_t)jr * G + blockIdx.x] = s;
+  }
+}
+
+// Interleaved FP32 sets with an even number R of right-hand sides: a thread
+// reads 16-byte pairs (two consecutive right-hand sides of one entry) of w
+// once per JB basis vectors and of each of those vectors; partial as k_bdots.
+// blockDim is a multiple of R/2 and the chunks are multiples of blockDim, so a
+// thread always holds the same pair of right-hand sides.
+template <int JB, typename TV>
+__global__ void __launch_bounds__(256) k_bdots_pairs(const TV* __restrict__ V, size_t ldv, int nvec,
+                                                      const float4* __restrict__ w, size_t npairs, int R,
+                                                      double2* __restrict__ partial) {
+  extern __shared__ float red_s[];  // [blockDim][4 JB + 1]
+  const int G = gridDim.x, j0 = blockIdx.y * JB, Rh = R / 2, bd = blockDim.x, t = threadIdx.x;
+  const int nj = nvec - j0 < JB ? nvec - j0 : JB;
+  float acc[JB][4];
+#pragma unroll
+  for (int jj = 0; jj < JB; jj++) acc[jj][0] = acc[jj][1] = acc[jj][2] = acc[jj][3] = 0.f;
+  const size_t chunk = ((npairs + (size_t)G * bd - 1) / ((size_t)G * bd)) * bd;
+  const size_t beg = (size_t)blockIdx.x * chunk, end = beg + chunk < npairs ? beg + chunk : npairs;
+  for (size_t i = beg + t; i < end; i += bd) {
+    const float4 y = __ldg(w + i);
+#pragma unroll
+    for (int jj = 0; jj < JB; jj++) {
+      if (jj < nj) {
+        const float4 x = ld_pair(V + (size_t)(j0 + jj) * ldv, i);
+        acc[jj][0] += x.x * y.x + x.y * y.y;
+        acc[jj][1] += x.x * y.y - x.y * y.x;
+        acc[jj][2] += x.z * y.z + x.w * y.w;
+        acc[jj][3] += x.z * y.w - x.w * y.z;
+      }
+    }
+  }
+  const int S = 4 * JB + 1;
+#pragma unroll
+  for (int jj = 0; jj < JB; jj++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) red_s[t * S + jj * 4 + c] = acc[jj][c];
+  __syncthreads();
+  for (int o = t; o < nj * R; o += bd) {
+    const int jj = o / R, r = o - jj * R, q = r >> 1, h = r & 1;
+    float sre = 0.f, sim = 0.f;
+    for (int m = q; m < bd; m += Rh) {
+      sre += red_s[m * S + jj * 4 + 2 * h];
+      sim += red_s[m * S + jj * 4 + 2 * h + 1];
+    }
+    partial[((size_t)(j0 + jj) * R + r) * G + blockIdx.x] = make_double2(sre, sim);
+  }
+}
+
+// w(., r) += sign * sum_j coef[j * R + r] V_j(., r) for interleaved FP32 w with
+// an even number of right-hand sides, V FP32 or FP16: 16-byte pairs of w, EPT
+// pairs per thread, the basis loop outside; optional per-rhs squared norms of
+// the result in npartial[r * G + cta].
+template <typename TV>
+__global__ void __launch_bounds__(256) k_bmaxpy_pairs(float2* __restrict__ w, const TV* __restrict__ V, size_t ldv,
+                                                       int nvec, const double2* __restrict__ coef, size_t npairs, int R,
+                                                       float sign, double2* __restrict__ npartial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sc = reinterpret_cast<float2*>(smem_raw);  // [nvec][R], times sign
+  __shared__ double2 red[256];
+  const int G = gridDim.x, bd = blockDim.x, Rh = R / 2, q = threadIdx.x % Rh;
+  for (int k = threadIdx.x; k < nvec * R; k += bd) sc[k] = make_float2(sign * (float)coef[k].x, sign * (float)coef[k].y);
+  __syncthreads();
+  const int EPT = 4;
+  const size_t span = (size_t)bd * EPT;
+  float4* w4 = reinterpret_cast<float4*>(w);
+  float nn0 = 0.f, nn1 = 0.f;
+  for (size_t base = (size_t)blockIdx.x * span; base < npairs; base += (size_t)G * span) {
+    float4 acc[EPT];
+    bool in[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; u++) {
+      const size_t i = base + threadIdx.x + (size_t)u * bd;
+      in[u] = i < npairs;
+      acc[u] = in[u] ? w4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll 2
+    for (int j = 0; j < nvec; j++) {
+      const TV* vj = V + (size_t)j * ldv;
+      const float2 c0 = sc[j * R + 2 * q], c1 = sc[j * R + 2 * q + 1];
+#pragma unroll
+      for (int u = 0; u < EPT; u++) {
+        if (!in[u]) continue;
+        const float4 v = ld_pair(vj, base + threadIdx.x + (size_t)u * bd);
+        acc[u].x += c0.x * v.x - c0.y * v.y;
+        acc[u].y += c0.x * v.y + c0.y * v.x;
+        acc[u].z += c1.x * v.z - c1.y * v.w;
+        acc[u].w += c1.x * v.w + c1.y * v.z;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EPT; u++) {
+      if (!in[u]) continue;
+      w4[base + threadIdx.x + (size_t)u * bd] = acc[u];
+      nn0 += acc[u].x * acc[u].x + acc[u].y * acc[u].y;
+      nn1 += acc[u].z * acc[u].z + acc[u].w * acc[u].w;
+    }
+  }
+  if (npartial) {
+    red[threadIdx.x] = make_double2(nn0, nn1);
+    __syncthreads();
+    if ((int)threadIdx.x < Rh) {
+      double s0 = 0, s1 = 0;
+      for (int m = threadIdx.x; m < bd; m += Rh) {
+        s0 += red[m].x;
+        s1 += red[m].y;
+      }
+      npartial[(size_t)(2 * threadIdx.x) * G + blockIdx.x] = make_double2(s0, 0);
+      npartial[(size_t)(2 * threadIdx.x + 1) * G + blockIdx.x] = make_double2(s1, 0);
+    }
   }
 }
 
@@ -302,25 +426,93 @@ static const double2* coef_to_device(Blas* b, const double2* vals, size_t count,
   return d;
 }
 
-#define DISPATCH_TYPES(TV, TW, CALL)                                                 \
-  do {                                                                               \
-    if ((TV) == 1 && (TW) == 1) { typedef float2 A; typedef float2 B; CALL; }        \
-    else if ((TV) == 0 && (TW) == 0) { typedef double2 A; typedef double2 B; CALL; } \
-    else if ((TV) == 1 && (TW) == 0) { typedef float2 A; typedef double2 B; CALL; }  \
-    else { typedef double2 A; typedef float2 B; CALL; }                              \
+#define DISPATCH_TYPES(TV, TW, CALL)                                                      \
+  do {                                                                                    \
+    if ((TV) == 1 && (TW) == 1) { typedef float2 A; typedef float2 B; CALL; }             \
+    else if ((TV) == 0 && (TW) == 0) { typedef double2 A; typedef double2 B; CALL; }      \
+    else if ((TV) == 1 && (TW) == 0) { typedef float2 A; typedef double2 B; CALL; }       \
+    else if ((TV) == 0 && (TW) == 1) { typedef double2 A; typedef float2 B; CALL; }       \
+    else if ((TV) == 2 && (TW) == 1) { typedef __half2 A; typedef float2 B; CALL; }       \
+    else if ((TV) == 1 && (TW) == 2) { typedef float2 A; typedef __half2 B; CALL; }       \
+    else throw Error(DDTM_ERR_ARG, "internal: unsupported vector type combination");     \
   } while (0)
 
+static double set_bytes(const VSet& v) {
+  return (double)v.n * v.R * (v.type == 0 ? 16 : v.type == 1 ? 8 : 4);
+}
+static const char* fam(const VSet& w, const char* coarse, const char* fine) { return w.inter ? coarse : fine; }
+
+static const int DOTS_JB = 8;
+template <typename TV>
+static void maxpy_pairs_t(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev, double sign,
+                          double2* npart, int G, int bd, cudaStream_t st) {
+  static bool cfg = false;
+  if (!cfg) {
+    CK(cudaFuncSetAttribute(k_bmaxpy_pairs<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    cfg = true;
+  }
+  const size_t smem = (size_t)nvec * w.R * sizeof(float2);
+  k_bmaxpy_pairs<TV><<<G, bd, smem, st>>>((float2*)w.p, (const TV*)V.p, ldv, nvec, coef_dev, w.n * w.R / 2, w.R,
+                                          (float)sign, npart);
+  CKL("bmaxpy_pairs");
+}
+static void launch_maxpy_pairs(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev,
+                               double sign, double2* npart, int G, int bd, cudaStream_t st) {
+  if (V.type == 2) maxpy_pairs_t<__half2>(w, V, ldv, nvec, coef_dev, sign, npart, G, bd, st);
+  else maxpy_pairs_t<float2>(w, V, ldv, nvec, coef_dev, sign, npart, G, bd, st);
+}
+static int maxpy_pairs_grid(const VSet& w, int bd) {
+  size_t npairs = w.n * w.R / 2, g = (npairs + (size_t)bd * 4 - 1) / ((size_t)bd * 4);
+  return (int)(g < 1 ? 1 : (g > 16384 ? 16384 : g));
+}
+static bool pairs_ok(const VSet& V, size_t ldv, const VSet& w) {
+  return w.inter && (V.type == 1 || V.type == 2) && w.type == 1 && w.R % 2 == 0 && lcm32(w.R / 2) <= 256 &&
+         ldv % 2 == 0 && ((uintptr_t)V.p & 15) == 0 && ((uintptr_t)w.p & 15) == 0;
+}
+static int pairs_block(const VSet& w) { return inter_block(w.R / 2); }
+// CTAs along the vector: about 1200 CTAs in all (8 per SM) whatever the
+// number of basis blocks, each thread taking at least 4 pairs
+static int pairs_grid(const VSet& w, int bd, int nvec) {
+  const size_t npairs = w.n * w.R / 2, jb = (size_t)(nvec + 7) / 8;
+  size_t g = (1216 + jb - 1) / jb, gmax = npairs / ((size_t)bd * 4);
+  if (g > gmax) g = gmax;
+  return (int)(g < 1 ? 1 : g);
+}
+template <typename TV>
+static void dots_pairs_t(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* partial, int G, int bd,
+                         cudaStream_t st) {
+  static bool cfg = false;
+  const size_t smem = (size_t)bd * (4 * DOTS_JB + 1) * sizeof(float);
+  if (!cfg) {
+    CK(cudaFuncSetAttribute(k_bdots_pairs<DOTS_JB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    cfg = true;
+  }
+  dim3 grid(G, (nvec + DOTS_JB - 1) / DOTS_JB);
+  k_bdots_pairs<DOTS_JB, TV><<<grid, bd, smem, st>>>((const TV*)V.p, ldv, nvec, (const float4*)w.p,
+                                                     w.n * w.R / 2, w.R, partial);
+  CKL("bdots_pairs");
+}
+static void launch_dots_pairs(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* partial, int G, int bd,
+                              cudaStream_t st) {
+  if (V.type == 2) dots_pairs_t<__half2>(V, ldv, nvec, w, partial, G, bd, st);
+  else dots_pairs_t<float2>(V, ldv, nvec, w, partial, G, bd, st);
+}
+
 void Blas::dots(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_host) {
-  ScopedTimer timer_("blas_dots", st);
+  ScopedTimer timer_(fam(w, "blas_dots_coarse", "blas_dots_fine"), st, nvec,
+                     (V.p == w.p && nvec == 1) ? set_bytes(w) : nvec * set_bytes(V) + set_bytes(w));
   const int R = w.R;
   if (nvec <= 0) return;
-  int bd = w.inter ? inter_block(R) : 256;
-  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  const bool pairs = pairs_ok(V, ldv, w);
+  int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
+  int G = pairs ? pairs_grid(w, bd, nvec) : grid_for(w.inter ? w.n * R : w.n, bd, 512);
   double2* partial = (double2*)pool->get("blas_partial", (size_t)nvec * R * G * sizeof(double2));
   double2* dres = (double2*)pool->get("blas_result", (size_t)nvec * R * sizeof(double2));
   dim3 grid(G, w.inter ? nvec : nvec * R);
   if (grid.y > 65535) throw Error(DDTM_ERR_ARG, "internal: too many vectors in one inner-product batch");
-  if (w.inter)
+  if (pairs)
+    launch_dots_pairs(V, ldv, nvec, w, partial, G, bd, st);
+  else if (w.inter)
     DISPATCH_TYPES(V.type, w.type,
                    (k_bdots<A, B, true><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
   else
@@ -357,16 +549,19 @@ static int maxpy_grid(size_t work, int bd) {
 
 void Blas::maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_host, double sign,
                  double* norms2_host) {
-  ScopedTimer timer_("blas_maxpy", st);
+  ScopedTimer timer_(fam(w, "blas_maxpy_coarse", "blas_maxpy_fine"), st, nvec, nvec * set_bytes(V) + 2 * set_bytes(w));
   const int R = w.R;
-  int bd = w.inter ? inter_block(R) : 256;
-  int G = maxpy_grid(w.inter ? w.n * R : w.n, bd);
+  const bool pairs = pairs_ok(V, ldv, w);
+  int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
+  int G = pairs ? maxpy_pairs_grid(w, bd) : maxpy_grid(w.inter ? w.n * R : w.n, bd);
   const double2* dc = coef_to_device(this, coef_host, (size_t)nvec * R, "blas_coef");
   double2* npart = norms2_host ? (double2*)pool->get("blas_npartial", (size_t)R * G * sizeof(double2)) : nullptr;
   size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
   if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");
   dim3 grid(G, w.inter ? 1 : R);
-  if (w.inter)
+  if (pairs)
+    launch_maxpy_pairs(w, V, ldv, nvec, dc, sign, npart, G, bd, st);
+  else if (w.inter)
     DISPATCH_TYPES(V.type, w.type,
                    (maxpy_launch<A, B, true>(grid, bd, smem, st, (B*)w.p, (const A*)V.p, ldv, nvec, dc, w.n, R, sign, npart)));
   else
@@ -400,7 +595,7 @@ static void elementwise_grid(const VSet& y, int* bd, dim3* grid) {
 }
 
 void Blas::axpby(const double2* a_host, const VSet& x, const double2* b_host, const VSet& y) {
-  ScopedTimer timer_("blas_axpby", st);
+  ScopedTimer timer_("blas_axpby", st, 1, set_bytes(x) + 2 * set_bytes(y));
   const int R = y.R;
   std::vector<double2> ab(2 * (size_t)R);
   for (int r = 0; r < R; r++) { ab[r] = a_host[r]; ab[R + r] = b_host[r]; }
@@ -416,15 +611,19 @@ void Blas::axpby(const double2* a_host, const VSet& x, const double2* b_host, co
 }
 
 void Blas::dots_dev(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_dev) {
-  ScopedTimer timer_("blas_dots", st);
+  ScopedTimer timer_(fam(w, "blas_dots_coarse", "blas_dots_fine"), st, nvec,
+                     (V.p == w.p && nvec == 1) ? set_bytes(w) : nvec * set_bytes(V) + set_bytes(w));
   const int R = w.R;
   if (nvec <= 0) return;
-  int bd = w.inter ? inter_block(R) : 256;
-  int G = grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  const bool pairs = pairs_ok(V, ldv, w);
+  int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
+  int G = pairs ? pairs_grid(w, bd, nvec) : grid_for(w.inter ? w.n * R : w.n, bd, 512);
   double2* partial = (double2*)pool->get("blas_partial_dev", (size_t)nvec * R * G * sizeof(double2));
   dim3 grid(G, w.inter ? nvec : nvec * R);
   if (grid.y > 65535) throw Error(DDTM_ERR_ARG, "internal: too many vectors in one inner-product batch");
-  if (w.inter)
+  if (pairs)
+    launch_dots_pairs(V, ldv, nvec, w, partial, G, bd, st);
+  else if (w.inter)
     DISPATCH_TYPES(V.type, w.type,
                    (k_bdots<A, B, true><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
   else
@@ -437,15 +636,18 @@ void Blas::dots_dev(const VSet& V, size_t ldv, int nvec, const VSet& w, double2*
 
 void Blas::maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev, double sign,
                      double2* norms2_dev) {
-  ScopedTimer timer_("blas_maxpy", st);
+  ScopedTimer timer_(fam(w, "blas_maxpy_coarse", "blas_maxpy_fine"), st, nvec, nvec * set_bytes(V) + 2 * set_bytes(w));
   const int R = w.R;
-  int bd = w.inter ? inter_block(R) : 256;
-  int G = maxpy_grid(w.inter ? w.n * R : w.n, bd);
+  const bool pairs = pairs_ok(V, ldv, w);
+  int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
+  int G = pairs ? maxpy_pairs_grid(w, bd) : maxpy_grid(w.inter ? w.n * R : w.n, bd);
   double2* npart = norms2_dev ? (double2*)pool->get("blas_npartial_dev", (size_t)R * G * sizeof(double2)) : nullptr;
   size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
   if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");
   dim3 grid(G, w.inter ? 1 : R);
-  if (w.inter)
+  if (pairs)
+    launch_maxpy_pairs(w, V, ldv, nvec, coef_dev, sign, npart, G, bd, st);
+  else if (w.inter)
     DISPATCH_TYPES(V.type, w.type,
                    (maxpy_launch<A, B, true>(grid, bd, smem, st, (B*)w.p, (const A*)V.p, ldv, nvec, coef_dev, w.n, R, sign, npart)));
   else
@@ -459,7 +661,7 @@ void Blas::maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const d
 }
 
 void Blas::scale_dev(const double2* a_dev, const VSet& x, const VSet& y) {
-  ScopedTimer timer_("blas_scale", st);
+  ScopedTimer timer_("blas_scale", st, 1, set_bytes(x) + set_bytes(y));
   const int R = y.R;
   int bd;
   dim3 grid;
@@ -495,46 +697,66 @@ __global__ void k_arnoldi_start(ArnoldiDev a, const double2* __restrict__ nr2) {
   a.scale[r] = make_double2(beta > 0 ? 1.0 / beta : 0.0, 0);
 }
 
+// Column j of R lockstep Arnoldi processes: ARB systems per CTA.  The whole
+// CTA first stages the new column (h, + h2) and the previous rotations in
+// shared memory with independent loads, then one thread per system runs the
+// sequential rotations from shared memory.  T = float for loose tolerances
+// (the rotations are a dependent chain and FP64 latency is high on this GPU),
+// double otherwise.
+static const int ARB = 8;
 template <typename T>
-__global__ void k_arnoldi_step(ArnoldiDev a, int j, const double2* __restrict__ h, const double2* __restrict__ h2,
-                               const double2* __restrict__ hn2) {
-  // one thread per system; its Hessenberg column (j + 2 entries) is kept in
-  // shared memory so the sequential rotations do not wait on global loads;
-  // T = float for loose tolerances (the rotations are a long dependent chain,
-  // and FP64 latency is high on this GPU), double otherwise
+__global__ void __launch_bounds__(128) k_arnoldi_step(ArnoldiDev a, int j, const double2* __restrict__ h,
+                                                      const double2* __restrict__ h2, const double2* __restrict__ hn2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* col = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)threadIdx.x * (j + 2);
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.R) return;
-  const int m = a.m, R = a.R;
-  double2* H = a.H + (size_t)r * (m + 1) * m;
-  for (int i = 0; i <= j; i++) {
-    double2 v = h[(size_t)i * R + r];
-    if (h2) { v.x += h2[(size_t)i * R + r].x; v.y += h2[(size_t)i * R + r].y; }
-    col[i] = cplx<T>((T)v.x, (T)v.y);
+  const int m = a.m, R = a.R, r0 = blockIdx.x * ARB;
+  const int nb = R - r0 < ARB ? R - r0 : ARB;
+  cplx<T>* col = reinterpret_cast<cplx<T>*>(smem_raw);  // [ARB][j + 2]
+  cplx<T>* cs = col + (size_t)ARB * (j + 2);             // [ARB][j]
+  cplx<T>* sn = cs + (size_t)ARB * j;                    // [ARB][j]
+  for (int k = threadIdx.x; k < (j + 1) * nb; k += blockDim.x) {
+    const int i = k / nb, rr = k - i * nb;
+    double2 v = h[(size_t)i * R + r0 + rr];
+    if (h2) {
+      const double2 v2 = h2[(size_t)i * R + r0 + rr];
+      v.x += v2.x;
+      v.y += v2.y;
+    }
+    col[(size_t)rr * (j + 2) + i] = cplx<T>((T)v.x, (T)v.y);
   }
-  double hn = sqrt(hn2[r].x);
-  col[j + 1] = cplx<T>((T)hn, 0);
-  const double2* csr = a.cs + (size_t)r * m;
-  const double2* snr = a.sn + (size_t)r * m;
+  for (int k = threadIdx.x; k < j * nb; k += blockDim.x) {
+    const int rr = k / j, i = k - rr * j;
+    const double2 c = a.cs[(size_t)(r0 + rr) * m + i], sv = a.sn[(size_t)(r0 + rr) * m + i];
+    cs[(size_t)rr * j + i] = cplx<T>((T)c.x, (T)c.y);
+    sn[(size_t)rr * j + i] = cplx<T>((T)sv.x, (T)sv.y);
+  }
+  __syncthreads();
+  const int rr = threadIdx.x;
+  if (rr >= nb) return;
+  const int r = r0 + rr;
+  cplx<T>* cl = col + (size_t)rr * (j + 2);
+  const cplx<T>* csr = cs + (size_t)rr * j;
+  const cplx<T>* snr = sn + (size_t)rr * j;
+  const double hn = sqrt(hn2[r].x);
+  cl[j + 1] = cplx<T>((T)hn, 0);
   for (int i = 0; i < j; i++) {
-    cplx<T> c((T)csr[i].x, (T)csr[i].y), s((T)snr[i].x, (T)snr[i].y);
-    cplx<T> x = col[i], y = col[i + 1];
-    col[i] = conj(c) * x + conj(s) * y;
-    col[i + 1] = c * y - s * x;
+    const cplx<T> c = csr[i], sv = snr[i];
+    const cplx<T> x = cl[i], y = cl[i + 1];
+    cl[i] = conj(c) * x + conj(sv) * y;
+    cl[i + 1] = c * y - sv * x;
   }
-  cplx<double> d((double)col[j].re, (double)col[j].im);
+  cplx<double> d((double)cl[j].re, (double)cl[j].im);
   double rho = sqrt(norm2(d) + hn * hn);
   cplx<double> c = rho > 0 ? cplx<double>(d.re / rho, d.im / rho) : cplx<double>(1, 0);
-  cplx<double> s = rho > 0 ? cplx<double>(hn / rho, 0) : cplx<double>(0, 0);
+  cplx<double> sv = rho > 0 ? cplx<double>(hn / rho, 0) : cplx<double>(0, 0);
   a.cs[(size_t)r * m + j] = zd2(c);
-  a.sn[(size_t)r * m + j] = zd2(s);
-  col[j] = cplx<T>((T)rho, 0);
-  col[j + 1] = cplx<T>(0, 0);
-  for (int i = 0; i <= j + 1; i++) H[(size_t)i * m + j] = make_double2((double)col[i].re, (double)col[i].im);
+  a.sn[(size_t)r * m + j] = zd2(sv);
+  cl[j] = cplx<T>((T)rho, 0);
+  cl[j + 1] = cplx<T>(0, 0);
+  double2* H = a.H + (size_t)r * (m + 1) * m;
+  for (int i = 0; i <= j + 1; i++) H[(size_t)i * m + j] = make_double2((double)cl[i].re, (double)cl[i].im);
   double2* g = a.g + (size_t)r * (m + 1);
   cplx<double> gj = zc2(g[j]);
-  g[j + 1] = zd2(-(s * gj));
+  g[j + 1] = zd2(-(sv * gj));
   g[j] = zd2(conj(c) * gj);
   double e = sqrt(norm2(zc2(g[j + 1])));
   a.est[r] = a.bn[r] > 0 ? e / a.bn[r] : 0.0;
@@ -564,23 +786,23 @@ void launch_arnoldi_start(const ArnoldiDev& a, const double2* nr2, cudaStream_t 
 void launch_arnoldi_step(const ArnoldiDev& a, int j, const double2* h, const double2* h2, const double2* hn2,
                          cudaStream_t st, bool fp32) {
   ScopedTimer timer_("arnoldi", st);
-  const int threads = a.R < 32 ? a.R : 32;  // at most 32 x (250 + 2) x 16 B of shared memory
+  const unsigned grid = (unsigned)((a.R + ARB - 1) / ARB);
   if (fp32) {
-    size_t smem = (size_t)threads * (j + 2) * sizeof(cplx<float>);
+    size_t smem = (size_t)ARB * (3 * j + 2) * sizeof(cplx<float>);
     static bool cfg = false;
     if (!cfg) {
       CK(cudaFuncSetAttribute(k_arnoldi_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       cfg = true;
     }
-    k_arnoldi_step<float><<<(a.R + threads - 1) / threads, threads, smem, st>>>(a, j, h, h2, hn2);
+    k_arnoldi_step<float><<<grid, 128, smem, st>>>(a, j, h, h2, hn2);
   } else {
-    size_t smem = (size_t)threads * (j + 2) * sizeof(cplx<double>);
+    size_t smem = (size_t)ARB * (3 * j + 2) * sizeof(cplx<double>);
     static bool cfg = false;
     if (!cfg) {
       CK(cudaFuncSetAttribute(k_arnoldi_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       cfg = true;
     }
-    k_arnoldi_step<double><<<(a.R + threads - 1) / threads, threads, smem, st>>>(a, j, h, h2, hn2);
+    k_arnoldi_step<double><<<grid, 128, smem, st>>>(a, j, h, h2, hn2);
   }
   CKL("arnoldi_step");
 }

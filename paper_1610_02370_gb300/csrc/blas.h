@@ -3,7 +3,8 @@
 // A "vector set" holds R right-hand sides of n complex entries each, either
 // interleaved (element (e, r) at e * R + r: coarse vectors) or separate
 // (element (e, r) at r * n + e: fine fields).  Type tags: 0 = double2 (FP64
-// complex), 1 = float2 (FP32 complex).  A basis of nvec sets lies at V + j*ldv
+// complex), 1 = float2 (FP32 complex), 2 = __half2 (FP16 complex storage,
+// FP32 arithmetic; paired with FP32 sets only).  A basis of nvec sets lies at V + j*ldv
 // (ldv in complex elements).  Every inner product accumulates in FP64 and is
 // reduced in a fixed order (deterministic).  Results that come back to the
 // host synchronise the stream; coefficients travel through a pinned ring of
@@ -18,7 +19,7 @@ namespace ddtm {
 
 struct VSet {
   void* p;
-  int type;     // 0 double2, 1 float2
+  int type;     // 0 double2, 1 float2, 2 __half2
   size_t n;     // complex entries per right-hand side
   int R;        // right-hand sides
   bool inter;   // interleaved (true) or separate (false)

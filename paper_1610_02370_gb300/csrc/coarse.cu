@@ -419,13 +419,13 @@ static void coarse_apply_d(const CoarseLevel& c, cplx<float>* y, const cplx<floa
 
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,
                               float sres, float sy, cudaStream_t st) {
-  ScopedTimer timer_("coarse_apply", st);
+  ScopedTimer timer_("coarse_apply", st, R);
   coarse_apply_d<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, mu_c, mode, sres, sy, st);
 }
 
 void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e, int R,
                              double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  ScopedTimer timer_("coarse_apply_odd_f32", st);
+  ScopedTimer timer_("coarse_apply_odd_f32", st, R);
   int no = (int)c.h_odd.size();
   coarse_apply_d<float2>(c, y_o, x_o, x_e, c.nbr_oe.as<int>(), c.odd.as<int>(), no, R, mu_c, mode, sres, sy, st);
 }
@@ -450,7 +450,7 @@ static void coarse_even_t(const CoarseLevel& c, cplx<float>* t, const cplx<float
 
 void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
                         float sh, cudaStream_t st) {
-  ScopedTimer timer_("coarse_even_f32", st);
+  ScopedTimer timer_("coarse_even_f32", st, R);
   if (R % 4 == 0) coarse_even_t<float2, 4>(c, t, rhs, v, R, sr, sh, st);
   else coarse_even_t<float2, 1>(c, t, rhs, v, R, sr, sh, st);
 }

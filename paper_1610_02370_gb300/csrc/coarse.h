@@ -54,7 +54,8 @@ bool tc_supported(int n);
 void build_coarse_images(CoarseLevel& c, cudaStream_t st);
 void build_inverse_images(CoarseLevel& c, cudaStream_t st);
 size_t tc_vector_image_bytes(const CoarseLevel& c, int nsites, int R);
-void launch_vector_image(const CoarseLevel& c, void* img, const cplx<float>* x, int nsites, int R, cudaStream_t st);
+// x: interleaved batch of type tag x_type (1 FP32, 2 FP16)
+void launch_vector_image(const CoarseLevel& c, void* img, const void* x, int x_type, int nsites, int R, cudaStream_t st);
 // One stencil pass over output slots idx < nout:
 //   acc = [self] A_self(idx) X_self(idx) + [hops] sum_d A_d(site) X_hop(tab[d-1][idx])
 //   y  = sy * yin + sres * (acc + i mu_c Gamma5_c xs)   (FP32, if y)
@@ -73,7 +74,8 @@ struct TcPass {
   int nout = 0;
   cplx<float>* y = nullptr;
   const cplx<float>* yin = nullptr;
-  const cplx<float>* xs = nullptr;
+  const void* xs = nullptr;  // self vector for the twist, type tag xs_type (1 FP32, 2 FP16)
+  int xs_type = 1;
   float sy = 0.f, sres = 1.f, mu_c = 0.f;
   void* yt = nullptr;
 };

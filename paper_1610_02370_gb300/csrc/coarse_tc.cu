@@ -21,8 +21,9 @@
 // columns of B for one site (b_bytes each).  One pipeline stage is then two
 // 1-D bulk copies (TMA engine) completing on one mbarrier.
 //
-// Kernel.  Persistent, one CTA per SM, 6 warps: warp 0 issues the bulk copies
-// of each (site, item) into a ring of stages, one thread of warp 1 issues the
+// Kernel.  Persistent, two CTAs per SM (one for batches wider than 16
+// right-hand sides), 6 warps: warp 0 issues the bulk copies of each
+// (site, item) into a ring of stages, one thread of warp 1 issues the
 // MMAs (accumulating a site's items in tensor memory, two accumulator buffers),
 // warps 2-5 read the accumulator rows back (tcgen05.ld), combine real and
 // imaginary parts, add the twist and the axpby terms and store FP32 and/or the
@@ -39,7 +40,12 @@
 namespace ddtm {
 
 static const int TC_MAXNS = 24;          // pipeline stages at most
-static const int TC_SMEM = 200 * 1024;   // dynamic shared memory budget
+// Dynamic shared memory per CTA.  One issuing thread per CTA caps a CTA near
+// 4-5 TB/s of bulk copies across the GPU, so two CTAs share each SM (each with
+// a shorter ring) where the epilogue's registers allow it.
+static const int TC_SMEM_1 = 200 * 1024;
+static const int TC_SMEM_2 = 108 * 1024;
+__host__ __device__ constexpr int tc_ctas_per_sm(int ngj) { return ngj <= 4 ? 2 : 1; }
 static const uint64_t TC_WAIT_NS = 2000000000ull;
 
 __host__ __device__ __forceinline__ size_t img_off(int row, int k, int sbo) {
@@ -86,9 +92,13 @@ __global__ void k_matrix_image(char* __restrict__ img, const float2* __restrict_
   *reinterpret_cast<uint4*>(img + b * a_bytes + img_off(row, 8 * h, sbo)) = *reinterpret_cast<const uint4*>(v);
 }
 
-// Vector images of interleaved complex vectors x[(s * n + k) * R + r]; one thread per
-// (site, column j = 2r + b, 8-wide k group).
-__global__ void k_vector_image(char* __restrict__ img, const float2* __restrict__ x, int nsites, int n, int R, int kpad,
+__device__ __forceinline__ float2 ld_f2(const float2* p, size_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float2 ld_f2(const __half2* p, size_t i) { return __half22float2(p[i]); }
+
+// Vector images of interleaved complex vectors x[(s * n + k) * R + r] (FP32 or
+// FP16); one thread per (site, column j = 2r + b, 8-wide k group).
+template <typename TX>
+__global__ void k_vector_image(char* __restrict__ img, const TX* __restrict__ x, int nsites, int n, int R, int kpad,
                                int sbo, int ngj, int b_bytes) {
   const int kg = kpad / 8, jc = 8 * ngj;
   const size_t per = (size_t)jc * kg;
@@ -103,7 +113,7 @@ __global__ void k_vector_image(char* __restrict__ img, const float2* __restrict_
     const int k = 8 * h + kk;
     float f = 0.f;
     if (k < n && r < R) {
-      const float2 z = __ldg(x + (s * n + k) * R + r);
+      const float2 z = ld_f2(x, (s * n + k) * R + r);
       f = (j & 1) ? z.y : z.x;
     }
     v[kk] = __float2half_rn(f);
@@ -124,7 +134,8 @@ struct TcArgs {
   int nout, self, hops;
   float2* y;            // y = sy * yin + sres * (acc + i mu_c Gamma5_c xs)   (FP32, optional)
   const float2* yin;
-  const float2* xs;
+  const void* xs;
+  int xs_half;
   float sy, sres, mu_c;
   char* yt;             // FP16 image of the same result (optional)
   int n, nv, R, r0, Rk; // columns r0 .. r0 + Rk - 1 of R right-hand sides
@@ -134,7 +145,7 @@ struct TcArgs {
 };
 
 template <int NGJ>
-__global__ void __launch_bounds__(192, 1) k_coarse_tc(const TcArgs a) {
+__global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * TC_MAXNS + 5];
   __shared__ uint32_t tmem_sh;
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_tc(const TcArgs a) {
           float im = (c ? pb + oa : ob + pa) * a.sres;
           const size_t o = ((size_t)idx * a.n + i) * a.R + r;
           if (a.xs) {
-            const float2 xv = a.xs[o];
+            const float2 xv = a.xs_half ? ld_f2((const __half2*)a.xs, o) : ld_f2((const float2*)a.xs, o);
             const float m = (i < a.nv ? a.mu_c : -a.mu_c) * a.sres;
             re -= m * xv.y;
             im += m * xv.x;
@@ -348,13 +359,21 @@ size_t tc_vector_image_bytes(const CoarseLevel& c, int nsites, int R) {
   return (size_t)nsites * tc_geom(c.n, R).b_bytes;
 }
 
-void launch_vector_image(const CoarseLevel& c, void* img, const cplx<float>* x, int nsites, int R, cudaStream_t st) {
-  ScopedTimer timer_("coarse_image", st);
+void launch_vector_image(const CoarseLevel& c, void* img, const void* x, int x_type, int nsites, int R, cudaStream_t st) {
   TcGeom t = tc_geom(c.n, R);
+  ScopedTimer timer_("coarse_image", st, R,
+                     (double)nsites * ((double)c.n * R * (x_type == 2 ? 4 : 8) + t.b_bytes));
   size_t tot = (size_t)nsites * 8 * t.ngj * (t.kpad / 8);
   if (!tot) return;
-  k_vector_image<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((char*)img, reinterpret_cast<const float2*>(x), nsites,
-                                                                c.n, R, t.kpad, t.sbo, t.ngj, t.b_bytes);
+  const unsigned grid = (unsigned)((tot + 255) / 256);
+  if (x_type == 2)
+    k_vector_image<__half2><<<grid, 256, 0, st>>>((char*)img, (const __half2*)x, nsites, c.n, R, t.kpad, t.sbo, t.ngj,
+                                                  t.b_bytes);
+  else if (x_type == 1)
+    k_vector_image<float2><<<grid, 256, 0, st>>>((char*)img, (const float2*)x, nsites, c.n, R, t.kpad, t.sbo, t.ngj,
+                                                 t.b_bytes);
+  else
+    throw Error(DDTM_ERR_ARG, "internal: vector image input type");
   CKL("vector_image");
 }
 
@@ -384,9 +403,15 @@ void build_inverse_images(CoarseLevel& c, cudaStream_t st) {
 }
 
 void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t st) {
-  ScopedTimer timer_(p.name, st);
-  if (p.nout <= 0) return;
   TcGeom t = tc_geom(c.n, R);
+  // algorithmic bytes: the matrix images, each input vector image once, the outputs
+  double bytes = (double)p.nout * ((p.self ? 1 : 0) + (p.hops ? 8 : 0)) * t.a_bytes;
+  bytes += (double)p.nout * t.b_bytes * ((p.self ? 1 : 0) + (p.hops && p.X_hop != p.X_self ? 1 : 0));
+  if (p.y) bytes += (double)p.nout * c.n * R * 8;
+  if (p.yt) bytes += (double)p.nout * t.b_bytes;
+  if (p.xs) bytes += (double)p.nout * c.n * R * (p.xs_type == 2 ? 4 : 8);
+  ScopedTimer timer_(p.name, st, R, bytes);
+  if (p.nout <= 0) return;
   for (int r0 = 0; r0 < R; r0 += 32) {
     const int Rk = R - r0 < 32 ? R - r0 : 32;
     const int ngj = (2 * Rk + 7) / 8, nmma = (2 * Rk + 15) / 16 * 16 < 16 ? 16 : (2 * Rk + 15) / 16 * 16;
@@ -404,7 +429,9 @@ void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t
     a.hops = p.hops ? 1 : 0;
     a.y = reinterpret_cast<float2*>(p.y);
     a.yin = reinterpret_cast<const float2*>(p.yin);
-    a.xs = reinterpret_cast<const float2*>(p.xs);
+    a.xs = p.xs;
+    if (p.xs && p.xs_type != 1 && p.xs_type != 2) throw Error(DDTM_ERR_ARG, "internal: twist vector type");
+    a.xs_half = p.xs_type == 2;
     a.sy = p.sy;
     a.sres = p.sres;
     a.mu_c = p.mu_c;
@@ -422,7 +449,8 @@ void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t
     a.nmma = nmma;
     a.bslot = nmma / 8 * t.sbo;
     a.apad = (128 - t.arows) / 8 * t.sbo;
-    a.ns = (TC_SMEM - a.apad) / (a.a_bytes + a.bslot);
+    const int cps = tc_ctas_per_sm(ngj), budget = cps == 2 ? TC_SMEM_2 : TC_SMEM_1;
+    a.ns = (budget - a.apad) / (a.a_bytes + a.bslot);
     if (a.ns > TC_MAXNS) a.ns = TC_MAXNS;
     if (a.ns < 2) throw Error(DDTM_ERR_ARG, "tensor-core coarse stencil: blocks too large for the stage ring");
     int tc = 32;
@@ -431,12 +459,12 @@ void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t
     a.idesc = ptx::idesc_f16_f32(128, nmma);
     a.err = c.tc_err.as<int>();
     const size_t smem = (size_t)a.ns * (a.a_bytes + a.bslot) + a.apad + 1024;
-    const int grid = p.nout < num_sms() ? p.nout : num_sms();
+    const int grid = p.nout < cps * num_sms() ? p.nout : cps * num_sms();
 #define TC_LAUNCH(K)                                                                                    \
   case K: {                                                                                           \
     static bool cfg = false;                                                                          \
     if (!cfg) {                                                                                       \
-      CK(cudaFuncSetAttribute(k_coarse_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM + 1024)); \
+      CK(cudaFuncSetAttribute(k_coarse_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_1 + 1024)); \
       cfg = true;                                                                                     \
     }                                                                                                 \
     k_coarse_tc<K><<<grid, 192, smem, st>>>(a);                                                       \

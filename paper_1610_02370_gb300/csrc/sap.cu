@@ -225,7 +225,7 @@ static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void*
 void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,
                      const void* clover, const void* sinv, const int* blocks, const int* zero_blocks, int nblocks,
                      int zero_x, int nmr, double mu, int nrhs, cudaStream_t s) {
-  ScopedTimer timer_(prec == PREC_F64 ? "sap_half_f64" : prec == PREC_F32 ? "sap_half_f32" : "sap_half_f16", s);
+  ScopedTimer timer_(prec == PREC_F64 ? "sap_half_f64" : prec == PREC_F32 ? "sap_half_f32" : "sap_half_f16", s, nrhs);
   if (prec == PREC_F64)
     launch_sap_half_t<PREC_F64>(g, x, xn, b, bn, links, clover, sinv, blocks, zero_blocks, nblocks, zero_x, nmr, mu, nrhs, s);
   else if (prec == PREC_F32)

@@ -129,7 +129,8 @@ static const void* P_for(ddtm_ctx* c, int prec, int* pprec) {
 
 // ---- batched GMRES on FP32 vectors --------------------------------------------------------
 // A(out, in) applies the operator to a batch of R interleaved vectors.
-typedef std::function<void(cplx<float>*, const cplx<float>*)> OpF32;
+// The input is a batch of vectors of type tag in_type (1 FP32, 2 FP16; see blas.h).
+typedef std::function<void(cplx<float>*, const void*, int)> OpF32;
 
 // Lockstep GMRES(m) with restarts for R systems A x_r = b_r (complex FP32
 // vectors of L entries each, interleaved; FP64 inner products).  Every
@@ -142,13 +143,19 @@ typedef std::function<void(cplx<float>*, const cplx<float>*)> OpF32;
 // as solved with x_r = 0).  An iteration already issued when the stop is seen
 // is discarded: the solution uses exactly the columns up to the converged one.
 // x is overwritten (zero start).  Returns the iteration count; relres[r] the
-// final estimates.
+// final estimates.  half_basis: the Krylov basis is stored in FP16 (the
+// residual, the new vector before normalisation and x stay FP32); every
+// product with it is formed in FP32, so the Arnoldi relation holds to FP16
+// rounding of the basis, far below the loose tolerances of the coarsest solve.
 static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float>* b, size_t L, int R, int m, int max_restarts,
-                   double tol, double* relres, const char* tag) {
+                   double tol, double* relres, const char* tag, bool half_basis) {
   Blas B(c->stream, &c->scratch, &c->ring);
   std::string t(tag);
   const size_t N = L * R;
-  cplx<float>* V = (cplx<float>*)c->scratch.get(t + "_V", (size_t)(m + 1) * N * sizeof(float2));
+  const int vt = half_basis ? 2 : 1;
+  const size_t vb = half_basis ? sizeof(__half2) : sizeof(float2);
+  char* V = (char*)c->scratch.get(t + (half_basis ? "_Vh" : "_V"), (size_t)(m + 1) * N * vb);
+  auto Vj = [&](int j) { return (void*)(V + (size_t)j * N * vb); };
   cplx<float>* w = (cplx<float>*)c->scratch.get(t + "_w", N * sizeof(float2));
   // device bookkeeping, one block of scratch
   size_t nH = (size_t)R * (m + 1) * m, ncs = (size_t)R * m, ng = (size_t)R * (m + 1), nh = (size_t)(m + 1) * R;
@@ -177,6 +184,7 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
 
   CK(cudaMemsetAsync(x, 0, N * sizeof(float2), c->stream));
   auto vs = [&](const void* p) { return VSet{(void*)p, 1, L, R, true}; };
+  auto vsb = [&](const void* p) { return VSet{(void*)p, vt, L, R, true}; };
   std::vector<double> bn(R);
   B.norms2(vs(b), bn.data());
   for (int r = 0; r < R; r++) bn[r] = sqrt(bn[r]);
@@ -198,32 +206,32 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
   int iters = 0;
   bool done = false;
   for (int cyc = 0; cyc <= max_restarts && !done; cyc++) {
+    // residual in w (FP32), then V_0 = w / ||w||
     if (cyc == 0) {
-      CK(cudaMemcpyAsync(V, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(w, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
     } else {
-      A(w, x);
-      CK(cudaMemcpyAsync(V, b, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
-      B.axpby(mone.data(), vs(w), one.data(), vs(V));
+      A(w, x, 1);
+      B.axpby(one.data(), vs(b), mone.data(), vs(w));
     }
-    B.dots_dev(vs(V), 0, 1, vs(V), nr2);
+    B.dots_dev(vs(w), 0, 1, vs(w), nr2);
     launch_arnoldi_start(ad, nr2, c->stream);
     fetch_est(0);
     CK(cudaEventSynchronize(ev[0]));
     for (int r = 0; r < R; r++) est[r] = est_h[r];
     if (all_done(est.data())) break;
-    B.scale_dev(ad.scale, vs(V), vs(V));
+    B.scale_dev(ad.scale, vs(w), vsb(Vj(0)));
     int k = 0;
     for (int j = 0; j < m; j++) {
-      A(w, V + (size_t)j * N);
-      B.dots_dev(vs(V), N, j + 1, vs(w), h);
-      B.maxpy_dev(vs(w), vs(V), N, j + 1, h, -1.0, reorth ? nullptr : nr2);
+      A(w, Vj(j), vt);
+      B.dots_dev(vsb(V), N, j + 1, vs(w), h);
+      B.maxpy_dev(vs(w), vsb(V), N, j + 1, h, -1.0, reorth ? nullptr : nr2);
       if (reorth) {
-        B.dots_dev(vs(V), N, j + 1, vs(w), h2);
-        B.maxpy_dev(vs(w), vs(V), N, j + 1, h2, -1.0, nr2);
+        B.dots_dev(vsb(V), N, j + 1, vs(w), h2);
+        B.maxpy_dev(vs(w), vsb(V), N, j + 1, h2, -1.0, nr2);
       }
       launch_arnoldi_step(ad, j, h, reorth ? h2 : nullptr, nr2, c->stream, tol >= 1e-3);
       fetch_est(j & 1);
-      if (j < m - 1) B.scale_dev(ad.scale, vs(w), vs(V + (size_t)(j + 1) * N));  // V_{j+1} = w / ||w||
+      if (j < m - 1) B.scale_dev(ad.scale, vs(w), vsb(Vj(j + 1)));  // V_{j+1} = w / ||w||
       iters++;
       k = j + 1;
       if (j >= 1) {  // estimates of the previous iteration
@@ -245,7 +253,7 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
       done = all_done(est.data());
     }
     launch_arnoldi_solve(ad, k, y, c->stream);
-    B.maxpy_dev(vs(x), vs(V), N, k, y, +1.0, nullptr);
+    B.maxpy_dev(vs(x), vsb(V), N, k, y, +1.0, nullptr);
   }
   for (int r = 0; r < R; r++) relres[r] = est[r];
   return iters;
@@ -280,8 +288,8 @@ int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full,
     char* ht = (char*)c->scratch.get("ceo_ht", img_e);
     char* tt = (char*)c->scratch.get("ceo_tt", img_e);
     const size_t ab = tc_geom(L.n, 1).a_bytes;
-    Dhat = [&, vt, ht, tt, ab](cplx<float>* out, const cplx<float>* in) {
-      launch_vector_image(L, vt, in, (int)no, Rc, c->stream);
+    Dhat = [&, vt, ht, tt, ab](cplx<float>* out, const void* in, int in_type) {
+      launch_vector_image(L, vt, in, in_type, (int)no, Rc, c->stream);
       TcPass h;  // ht = D_eo in
       h.name = "coarse_tc_hop_even";
       h.hops = true;
@@ -316,16 +324,20 @@ int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full,
       o.nout = (int)no;
       o.y = out;
       o.xs = in;
+      o.xs_type = in_type;
       o.mu_c = (float)mu_c;
       launch_coarse_tc(L, o, Rc, c->stream);
     };
   } else {
-    Dhat = [&](cplx<float>* out, const cplx<float>* in) {
+    Dhat = [&](cplx<float>* out, const void* in_v, int in_type) {
+      if (in_type != 1) throw Error(DDTM_ERR_ARG, "internal: FP32 coarse stencil takes FP32 vectors");
+      const cplx<float>* in = (const cplx<float>*)in_v;
       launch_coarse_even(L, tA, nullptr, in, Rc, 0.f, -1.f, c->stream);               // tA = -D_ee^-1 D_eo in
       launch_coarse_apply_odd(L, out, in, tA, Rc, mu_c, 3, 1.f, 0.f, c->stream);      // out = D_oo in + D_oe tA
     };
   }
-  int it = gmres_b(c, Dhat, xo, bo, no * n, Rc, restart, max_restarts, tol, relres, "cgm");
+  // FP16 Krylov basis with the tensor-core stencil (which reads FP16 operands anyway)
+  int it = gmres_b(c, Dhat, xo, bo, no * n, Rc, restart, max_restarts, tol, relres, "cgm", L.prec == PREC_F16);
   launch_coarse_even(L, te, be, xo, Rc, 1.f, -1.f, c->stream);  // phi_e = D_ee^-1 (eta_e - D_eo phi_o)
   launch_parity_copy(L, 0, te, x_full, Rc, 1, c->stream);
   launch_parity_copy(L, 1, xo, x_full, Rc, 1, c->stream);
@@ -783,7 +795,7 @@ int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs
   }
   if (L.prec == PREC_F16) {
     char* xt = (char*)ctx->scratch.get("abi_ct", tc_vector_image_bytes(L, L.Nc, nrhs));
-    launch_vector_image(L, xt, xv, L.Nc, nrhs, ctx->stream);
+    launch_vector_image(L, xt, xv, 1, L.Nc, nrhs, ctx->stream);
     TcPass f;
     f.name = "coarse_tc_full";
     f.self = f.hops = true;

@@ -10,14 +10,22 @@ namespace {
 struct Rec {
   const char* name;
   cudaEvent_t a, b;
+  long units;
+  double bytes;
+};
+struct Acc {
+  long launches = 0, units = 0;
+  double ms = 0, bytes = 0;
 };
 struct State {
   bool on = false;
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
-  std::map<std::string, std::pair<long, double>> acc;
+  std::map<std::string, Acc> acc;
   const char* cur = nullptr;
   cudaEvent_t cur_a = nullptr;
+  long cur_units = 0;
+  double cur_bytes = 0;
 };
 State& S() {
   static State s;
@@ -41,8 +49,10 @@ void flush() {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
     auto& v = s.acc[r.name];
-    v.first += 1;
-    v.second += ms;
+    v.launches += 1;
+    v.units += r.units;
+    v.bytes += r.bytes;
+    v.ms += ms;
     s.pool.push_back(r.a);
     s.pool.push_back(r.b);
   }
@@ -65,19 +75,21 @@ std::string timer_report_json() {
   bool first = true;
   for (auto& kv : S().acc) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %ld, \"ms\": %.6f}", first ? "" : ", ", kv.first.c_str(),
-             kv.second.first, kv.second.second);
+    snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %ld, \"ms\": %.6f, \"units\": %ld, \"bytes\": %.0f}",
+             first ? "" : ", ", kv.first.c_str(), kv.second.launches, kv.second.ms, kv.second.units, kv.second.bytes);
     out += buf;
     first = false;
   }
   return out + "}";
 }
 
-ScopedTimer::ScopedTimer(const char* name, cudaStream_t s) : active(S().on), st(s) {
+ScopedTimer::ScopedTimer(const char* name, cudaStream_t s, long units, double bytes) : active(S().on), st(s) {
   if (!active) return;
   State& g = S();
   if (g.pending.size() > 20000) flush();
   g.cur = name;
+  g.cur_units = units;
+  g.cur_bytes = bytes;
   g.cur_a = get_event();
   CK(cudaEventRecord(g.cur_a, s));
 }
@@ -86,7 +98,7 @@ ScopedTimer::~ScopedTimer() {
   if (!active) return;
   State& g = S();
   cudaEvent_t b = get_event();
-  if (cudaEventRecord(b, st) == cudaSuccess) g.pending.push_back(Rec{g.cur, g.cur_a, b});
+  if (cudaEventRecord(b, st) == cudaSuccess) g.pending.push_back(Rec{g.cur, g.cur_a, b, g.cur_units, g.cur_bytes});
 }
 
 }  // namespace ddtm

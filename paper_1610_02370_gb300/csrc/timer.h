@@ -14,12 +14,16 @@ namespace ddtm {
 bool timer_on();
 void timer_enable(bool on);
 void timer_reset();
-std::string timer_report_json();  // {"name": {"launches": n, "ms": t}, ...}
+// {"name": {"launches": n, "ms": t, "units": u, "bytes": b}, ...}
+std::string timer_report_json();
 
+// units: work items of the launch (right-hand sides or vectors it processes);
+// bytes: algorithmic memory traffic of the launch (every element it must read
+// or write, once), 0 where the caller does not state it
 struct ScopedTimer {
   bool active;
   cudaStream_t st;
-  ScopedTimer(const char* name, cudaStream_t s);
+  ScopedTimer(const char* name, cudaStream_t s, long units = 1, double bytes = 0);
   ~ScopedTimer();
 };
 

@@ -81,7 +81,7 @@ __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv,
 }
 
 void launch_build_P(const FineGeom& g, float2* P, const float2* tv, int nv, cudaStream_t st) {
-  ScopedTimer timer_("build_P", st);
+  ScopedTimer timer_("build_P", st, nv);
   int threads = ((g.Vb + 31) / 32) * 32;
   k_build_P<<<g.Nb * 2, threads, 0, st>>>(P, tv, nv, g.Vb, g.V);
   CKL("build_P");
@@ -244,14 +244,14 @@ static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cpl
 
 void launch_restrict(const FineGeom& g, int pin, cplx<float>* c, const void* psi, const float* pn, const void* P,
                      int pprec, int nv, int R, int Rs, cudaStream_t st) {
-  ScopedTimer timer_(pin == PREC_F16 ? "restrict_f16" : pin == PREC_F32 ? "restrict_f32" : "restrict_f64", st);
+  ScopedTimer timer_(pin == PREC_F16 ? "restrict_f16" : pin == PREC_F32 ? "restrict_f32" : "restrict_f64", st, R);
   if (pprec == PREC_F16) restrict_t<__half2>(g, pin, c, psi, pn, (const __half2*)P, nv, R, Rs, st);
   else restrict_t<float2>(g, pin, c, psi, pn, (const float2*)P, nv, R, Rs, st);
 }
 
 void launch_prolong(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const void* P, int pprec,
                     int nv, int R, int Rs, int add, cudaStream_t st) {
-  ScopedTimer timer_(pout == PREC_F16 ? "prolong_f16" : pout == PREC_F32 ? "prolong_f32" : "prolong_f64", st);
+  ScopedTimer timer_(pout == PREC_F16 ? "prolong_f16" : pout == PREC_F32 ? "prolong_f32" : "prolong_f64", st, R);
   if (pprec == PREC_F16) prolong_t<__half2>(g, pout, x, xn, e, (const __half2*)P, nv, R, Rs, add, st);
   else prolong_t<float2>(g, pout, x, xn, e, (const float2*)P, nv, R, Rs, add, st);
 }

@@ -1,0 +1,96 @@
+"""Small drivers that run one kernel family of libddtm on a synthetic lattice,
+for timing and for profiling a single kernel in isolation.
+
+    python -m paper_1610_02370_gb300.kernel_bench coarse --dims 48 24 24 24 --nv 24 --nrhs 12 --reps 4
+    python -m paper_1610_02370_gb300.kernel_bench dslash --dims 64 32 32 32 --prec 1 --reps 10
+
+``coarse`` builds the aggregation from Gaussian test vectors (no setup
+iterations) and applies the coarse operator D_c (Sec. 2.3) to a batch of
+nrhs vectors; ``dslash`` applies D(mu) (Sec. 2.1) to one field.  Each prints
+one JSON line with the median time per call (CUDA events).
+"""
+
+import argparse
+import json
+import statistics
+
+import torch
+
+from . import ddtm, synth
+
+
+def _events(fn, reps):
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def coarse(args):
+    dims = tuple(args.dims)
+    U = synth.gauge_field(dims, args.eps, seed=0, device="cuda")
+    ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 0)
+    try:
+        ddtm.ddtm_load_gauge(ctx, U, args.kappa, args.csw)
+        p = ddtm.ddtm_get_params(ctx)
+        p.nv[0] = args.nv
+        p.coarse_prec = args.coarse_prec
+        ddtm.ddtm_set_params(ctx, p)
+        lat = tuple(dims)
+        v = synth.gaussian_vectors((args.nv,) + lat + (4, 3), seed=5, device="cuda")
+        ddtm.ddtm_set_test_vectors(ctx, 0, v, args.nv)
+        del v
+        cl = tuple(d // 4 for d in dims)
+        x = synth.gaussian_vectors((args.nrhs,) + cl + (2 * args.nv,), seed=6, device="cuda")
+        y = torch.zeros_like(x)
+        ms = _events(lambda: ddtm.ddtm_apply_Dc(ctx, 1, y, x, args.nrhs, 0.01), args.reps)
+        print(json.dumps({"kernel": "coarse", "dims": dims, "nv": args.nv, "nrhs": args.nrhs,
+                          "coarse_prec": args.coarse_prec, "ms_per_call": ms}))
+    finally:
+        ddtm.ddtm_destroy(ctx)
+
+
+def dslash(args):
+    dims = tuple(args.dims)
+    U = synth.gauge_field(dims, args.eps, seed=0, device="cuda")
+    ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 0)
+    try:
+        ddtm.ddtm_load_gauge(ctx, U, args.kappa, args.csw)
+        x = synth.gaussian_spinor(dims, seed=1, device="cuda")
+        fx = ddtm.ddtm_field_create(ctx, args.prec, 1)
+        fy = ddtm.ddtm_field_create(ctx, args.prec, 1)
+        ddtm.ddtm_field_import(ctx, fx, x)
+        ms = _events(lambda: ddtm.ddtm_apply_D_field(ctx, fy, fx, 0.01), args.reps)
+        print(json.dumps({"kernel": "dslash", "dims": dims, "prec": args.prec, "ms_per_call": ms}))
+        ddtm.ddtm_field_destroy(fx)
+        ddtm.ddtm_field_destroy(fy)
+    finally:
+        ddtm.ddtm_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["coarse", "dslash"])
+    ap.add_argument("--dims", type=int, nargs=4, default=[48, 24, 24, 24])
+    ap.add_argument("--eps", type=float, default=0.15)
+    ap.add_argument("--kappa", type=float, default=0.137)
+    ap.add_argument("--csw", type=float, default=1.5755)
+    ap.add_argument("--nv", type=int, default=24)
+    ap.add_argument("--nrhs", type=int, default=12)
+    ap.add_argument("--coarse-prec", type=int, default=2)
+    ap.add_argument("--prec", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=4)
+    args = ap.parse_args()
+    from . import build
+    build.build()
+    {"coarse": coarse, "dslash": dslash}[args.what](args)
+
+
+if __name__ == "__main__":
+    main()
