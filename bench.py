@@ -91,6 +91,23 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc):
     return None
 
 
+def algorithmic_flops(name, Vb, b, nv):
+    """Algorithmic FP32 flops of one launch of the compute-bound setup kernels
+    (None otherwise), per aggregate times the number of aggregates."""
+    n = 2 * nv
+    if name == "galerkin":
+        # D applied to the n columns of P on the aggregate and its faces (1920 flops per site),
+        # self block: n x n entries of 6 Vb complex products; hop block k: 6 Vb / b_k products
+        per = n * Vb * 1920 + 8 * n * n * 6 * Vb + sum(2 * 8 * n * n * 6 * Vb / bb for bb in b)
+        return per
+    if name == "build_P":
+        # two modified Gram-Schmidt passes over the nv vectors of each aggregate half (6 Vb entries)
+        m = 6 * Vb
+        per_half = 2 * (nv * (nv - 1) / 2 * 16 * m + nv * 8 * m)
+        return 2 * per_half
+    return None
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -100,6 +117,7 @@ def parse_args():
     ap.add_argument("--workload", default="32x32x32x64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     return ap.parse_args()
 
 
@@ -408,15 +426,28 @@ def main():
     launches = counts[dom]["launches"]
     avg_s = counts[dom]["ms"] / launches / 1000.0
     nbytes = bytes_per_launch(dom)
-    achieved = nbytes / avg_s / 1e9 if nbytes else None
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm if achieved else None, "traffic": None,
-                "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches / args.steps,
-                "bytes_per_launch": nbytes, "peak_source": peak_note}
+    fl = algorithmic_flops(dom, Vb, MG["block"], MG["nv"])
+    if fl:
+        # FP32 SIMT arithmetic: 152 SMs x 128 FMA lanes x 2 flops at the sampled SM clock
+        alu = 152 * 128 * 2 * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
+        per_launch = fl * Nc
+        achieved = per_launch / avg_s / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                    "frac": achieved / alu, "traffic": None, "share": counts[dom]["ms"] / total_ms,
+                    "launches_per_step": launches / args.steps, "flops_per_launch": per_launch,
+                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x sampled SM clock"}
+    else:
+        achieved = nbytes / avg_s / 1e9 if nbytes else None
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm if achieved else None, "traffic": None,
+                    "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches / args.steps,
+                    "bytes_per_launch": nbytes, "peak_source": peak_note}
     breakdown = {}
     for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"]):
         nb = bytes_per_launch(k)
+        fk = algorithmic_flops(k, Vb, MG["block"], MG["nv"])
         breakdown[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                        "tflops": fk * Nc / (v["ms"] / v["launches"] / 1000.0) / 1e12 if fk else None,
                         "units_per_step": v.get("units", v["launches"]) / args.steps,
                         "share": v["ms"] / total_ms,
                         "gbs": nb / (v["ms"] / v["launches"] / 1000.0) / 1e9 if nb else None}
@@ -444,6 +475,42 @@ def main():
             te = float(t.item())
         e2e = {"value": te / world, "unit": UNIT, "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
                "d2h_bytes_per_step": int(xh.numel() * 16)}
+
+    ddtm.ddtm_destroy(ctx)
+
+    # The plain FP64 method for comparison: FP64 outer FGMRES and SAP smoother,
+    # FP32 SIMT coarse operator, one right-hand side per solve.  One point
+    # source is solved and timed; 12 sequential solves cost 12 times that.
+    fp64 = None
+    if not args.no_fp64:
+        c64 = ddtm.ddtm_create(dims, MG["block"], 0)
+        ddtm.ddtm_set_stream(c64, stream.cuda_stream)
+        p = ddtm.ddtm_get_params(c64)
+        p.nv[0] = MG["nv"]
+        for k in ("n_setup", "post_smooth", "nmr", "outer_restart", "outer_tol"):
+            setattr(p, k, MG[k])
+        p.smoother_prec = ddtm.PREC_F64
+        p.coarse_prec = ddtm.PREC_F32
+        ddtm.ddtm_set_params(c64, p)
+        ddtm.ddtm_load_gauge(c64, U, wl["kappa"], wl["c_sw"])
+        b1 = b[0:1].contiguous()
+        x1 = torch.zeros_like(b1)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        barrier()
+        e0.record(stream)
+        ddtm.ddtm_setup(c64, mu, SEED)
+        e1.record(stream)
+        info, code = ddtm.ddtm_solve(c64, x1, b1, 1, mu)
+        e2.record(stream)
+        barrier()
+        t_setup, t_solve = e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3
+        seq = t_setup + NRHS * t_solve
+        fp64 = {"setup_s": t_setup, "solve_s_one_rhs": t_solve, "iters": info.iters, "max_relres": info.max_relres,
+                "converged": code == ddtm.OK, "sequential_12_rhs_s": seq,
+                "speedup_mixed_batched_vs_fp64_sequential": seq / value,
+                "method": "FP64 outer FGMRES and SAP smoother, FP32 SIMT coarse stencil, one rhs per solve; "
+                          "one point source timed, 12 sequential solves = setup + 12 x that time"}
+        ddtm.ddtm_destroy(c64)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -479,10 +546,10 @@ def main():
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "e2e": e2e,
+            "fp64_reference": fp64,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
-    ddtm.ddtm_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -87,8 +87,12 @@ typedef struct {
   int outer_max_iters;     /* cap on outer iterations over all restarts */
   double outer_tol;        /* relative residual ||b - D x|| / ||b||, 1e-10 */
   double restart_tol;      /* mixed-precision restart criterion, Table 1: 1e-6 */
-  int smoother_prec;       /* storage precision of SAP and transfer: DDTM_PREC_F16 or F32 */
-  int coarse_prec;         /* storage precision of coarse operators: DDTM_PREC_F32 or F16 */
+  int smoother_prec;       /* storage precision of SAP and transfer: DDTM_PREC_F16 or F32 (mixed-precision
+                              outer cycle in FP32), or DDTM_PREC_F64 (the whole fine level in FP64: the plain
+                              FP64 method; the coarse correction stays FP32) */
+  int coarse_prec;         /* coarse operator: DDTM_PREC_F32 (FP32 blocks, SIMT stencil) or DDTM_PREC_F16
+                              (FP16 operand images on the tensor cores, FP32 accumulation, FP16 Krylov
+                              basis in the coarsest GMRES) */
 } ddtm_params;
 
 /* Per-solve report (Tables 2-3 columns): iteration counts, residuals, times. */

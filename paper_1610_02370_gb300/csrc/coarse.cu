@@ -92,23 +92,44 @@ __global__ void k_galerkin(DS* __restrict__ Dc, const float2* __restrict__ P, Li
       for (int c = 0; c < 12; c++) y0[c * Vb + loc] = out[c] + (-0.5f) * acc[c];
     }
     __syncthreads();
-    for (int o = w; o < 9 * n; o += nw) {
-      const int d = o / n, row = o - d * n;
-      const int s = row / nv, i = row - s * nv;
-      cplx<float> acc(0, 0);
+    // projections: a warp takes GR rows of one block d (independent loads of
+    // GR rows of P per step), the lanes stride over the sites
+    const int GR = 4, ngr = (n + GR - 1) / GR;
+    for (int o = w; o < 9 * ngr; o += nw) {
+      const int d = o / ngr, r0 = (o - d * ngr) * GR;
+      cplx<float> acc[GR];
+      int sr[GR], ir[GR];
+#pragma unroll
+      for (int r = 0; r < GR; r++) {
+        acc[r] = cplx<float>(0, 0);
+        const int row = r0 + r < n ? r0 + r : n - 1;
+        sr[r] = row / nv;
+        ir[r] = row - sr[r] * nv;
+      }
       if (d == 0) {
         for (int comp = 0; comp < 6; comp++)
+#pragma unroll 4
           for (int loc = lane; loc < Vb; loc += 32)
-            cmac_conj(acc, ld(P + pix(A, s, i, comp, loc, nv, Vb)), y0[(6 * s + comp) * Vb + loc]);
+#pragma unroll
+            for (int r = 0; r < GR; r++)
+              cmac_conj(acc[r], ld(P + pix(A, sr[r], ir[r], comp, loc, nv, Vb)), y0[(6 * sr[r] + comp) * Vb + loc]);
       } else {
         const int k = d - 1;
         for (int comp = 0; comp < 6; comp++)
-          for (int q = f.off[k] + lane; q < f.off[k + 1]; q += 32)
-            cmac_conj(acc, ld(P + pix(A, s, i, comp, f.list[q], nv, Vb)), yf[(6 * s + comp) * nf + q]);
+#pragma unroll 2
+          for (int q = f.off[k] + lane; q < f.off[k + 1]; q += 32) {
+            const int fl = f.list[q];
+#pragma unroll
+            for (int r = 0; r < GR; r++)
+              cmac_conj(acc[r], ld(P + pix(A, sr[r], ir[r], comp, fl, nv, Vb)), yf[(6 * sr[r] + comp) * nf + q]);
+          }
       }
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      if (lane == 0) stD(Dc + (((size_t)A * 9 + d) * n + col) * n + row, acc);
+#pragma unroll
+      for (int r = 0; r < GR; r++) {
+        acc[r].re = warp_sum(acc[r].re);
+        acc[r].im = warp_sum(acc[r].im);
+        if (lane == 0 && r0 + r < n) stD(Dc + (((size_t)A * 9 + d) * n + col) * n + r0 + r, acc[r]);
+      }
     }
     __syncthreads();
   }

@@ -34,8 +34,8 @@ void validate_params(ddtm_ctx* c, const ddtm_params& p) {
     throw Error(DDTM_ERR_ARG, "invalid Krylov parameters");
   if (!(p.outer_tol > 0) || !(p.coarse_tol > 0) || !(p.delta > 0) || !(p.restart_tol > 0))
     throw Error(DDTM_ERR_ARG, "invalid tolerances");
-  if (p.smoother_prec != DDTM_PREC_F32 && p.smoother_prec != DDTM_PREC_F16)
-    throw Error(DDTM_ERR_ARG, "smoother_prec must be F32 or F16");
+  if (p.smoother_prec != DDTM_PREC_F64 && p.smoother_prec != DDTM_PREC_F32 && p.smoother_prec != DDTM_PREC_F16)
+    throw Error(DDTM_ERR_ARG, "smoother_prec must be F64, F32 or F16");
   if (p.coarse_prec != DDTM_PREC_F32 && p.coarse_prec != DDTM_PREC_F16)
     throw Error(DDTM_ERR_ARG, "coarse_prec must be F32 or F16");
   if (p.coarse_prec == DDTM_PREC_F16 && p.nv[0] > 32)
@@ -377,6 +377,9 @@ void mg_precondition(ddtm_ctx* c, int prec, void* z, float* zn, const void* v, c
 // the smoother precision: the flexible method uses exactly the stored Z_j for
 // both w = D Z_j and the update.  Hessenberg matrices and Givens rotations stay
 // on the device; the host reads the estimates one iteration behind.
+// With an FP64 smoother the cycle itself is FP64 (basis, w = D z, Gram-Schmidt)
+// and runs to the final target: the plain FP64 method, kept as the reference
+// for the mixed-precision solver (the coarse correction stays FP32).
 struct OuterResult {
   int iters = 0, restarts = 0;
   std::vector<double> relres;
@@ -389,30 +392,34 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
   Blas B(c->stream, &c->scratch, &c->ring);
   const int sp = p.smoother_prec, m = p.outer_restart;
   const size_t n = (size_t)g.V * 12;  // complex entries of one fine field
-  const size_t fb = fine_field_bytes(g, sp), f32 = n * 8;
-  ensure_fine_prec(c, PREC_F32);
-  float2* V = (float2*)c->scratch.get("out_V", (size_t)(m + 1) * R * f32);
+  const size_t fb = fine_field_bytes(g, sp);
+  // cycle precision: FP32 (mixed precision) or, with an FP64 smoother, FP64 throughout
+  const bool c64 = sp == PREC_F64;
+  const int cp = c64 ? PREC_F64 : PREC_F32, vt = c64 ? 0 : 1;
+  const size_t cb = n * (c64 ? 16 : 8);  // bytes of one cycle-precision field
+  ensure_fine_prec(c, cp);
+  char* V = (char*)c->scratch.get(c64 ? "out_V64" : "out_V", (size_t)(m + 1) * R * cb);
   char* Z = (char*)c->scratch.get("out_Z", (size_t)m * R * fb);
   float* Zn = (float*)c->scratch.get("out_Zn", (size_t)m * R * g.V * sizeof(float));
-  float2* w = (float2*)c->scratch.get("out_w", (size_t)R * f32);
-  float2* t32 = (float2*)c->scratch.get("out_t32", (size_t)R * f32);
+  char* w = (char*)c->scratch.get(c64 ? "out_w64" : "out_w", (size_t)R * cb);
+  char* t32 = (char*)c->scratch.get(c64 ? "out_t64c" : "out_t32", (size_t)R * cb);
   double* r64 = (double*)c->scratch.get("out_r64", (size_t)R * n * 16);
   char* vsb = (char*)c->scratch.get("out_vs", (size_t)R * fb);
   float* vsn = (float*)c->scratch.get("out_vsn", (size_t)R * g.V * sizeof(float));
   auto Zj = [&](int j) { return (void*)(Z + (size_t)j * R * fb); };
   auto Zjn = [&](int j) { return sp == PREC_F16 ? Zn + (size_t)j * R * g.V : (float*)nullptr; };
-  auto Vj = [&](int j) { return V + (size_t)j * R * n; };
+  auto Vj = [&](int j) { return (void*)(V + (size_t)j * R * cb); };
   auto s64 = [&](const double* p0) { return VSet{(void*)p0, 0, n, R, false}; };
-  auto s32 = [&](const float2* p0) { return VSet{(void*)p0, 1, n, R, false}; };
+  auto sc_ = [&](const void* p0) { return VSet{(void*)p0, vt, n, R, false}; };
   auto D64 = [&](double* out, const double* in) {
     for (int r = 0; r < R; r++)
       launch_dslash(g, PREC_F64, out + 2 * (size_t)r * n, nullptr, in + 2 * (size_t)r * n, nullptr, c->links[0].p,
                     c->clover[0].p, mu, c->stream);
   };
-  auto D32 = [&](float2* out, const float2* in) {
+  auto Dcyc = [&](void* out, const void* in) {
     for (int r = 0; r < R; r++)
-      launch_dslash(g, PREC_F32, out + (size_t)r * n, nullptr, in + (size_t)r * n, nullptr, c->links[PREC_F32].p,
-                    c->clover[PREC_F32].p, mu, c->stream);
+      launch_dslash(g, cp, (char*)out + (size_t)r * cb, nullptr, (const char*)in + (size_t)r * cb, nullptr,
+                    c->links[cp].p, c->clover[cp].p, mu, c->stream);
   };
   // device bookkeeping
   size_t nH = (size_t)R * (m + 1) * m, ncs = (size_t)R * m, ng = (size_t)R * (m + 1), nh = (size_t)(m + 1) * R;
@@ -474,17 +481,18 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
       done = done && res.relres[r] <= p.outer_tol;
       sc[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
       // stop the cycle at restart_tol relative to its start, or at the final target
-      thr[r] = beta[r] > 0 ? std::max(p.restart_tol, 0.5 * p.outer_tol * bn[r] / beta[r]) : 1.0;
+      // (an FP64 cycle needs no restarts for precision: it runs to the target)
+      const double target = 0.5 * p.outer_tol * bn[r] / beta[r];
+      thr[r] = beta[r] > 0 ? (c64 ? target : std::max(p.restart_tol, target)) : 1.0;
     }
     if (done) {
       res.converged = true;
       break;
     }
     if (res.iters >= p.outer_max_iters) break;
-    // V_0 = r / beta in FP32; the device Arnoldi state starts from ||V_0|| (= 1)
-    // V_0 = r / beta in FP32; the device state starts with g_0 = beta and
-    // estimates relative to beta (so y is the correction for r itself)
-    B.axpby(sc.data(), s64(r64), zero.data(), s32(Vj(0)));
+    // V_0 = r / beta in the cycle precision; the device state starts with
+    // g_0 = beta and estimates relative to beta (so y is the correction for r itself)
+    B.axpby(sc.data(), s64(r64), zero.data(), sc_(Vj(0)));
     {
       double* hb = (double*)c->scratch_host("out_beta", 3 * (size_t)R * sizeof(double));
       for (int r = 0; r < R; r++) {
@@ -502,29 +510,29 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
     for (int j = 0; j < m; j++) {
       const void* vin = Vj(j);
       const float* vinn = nullptr;
-      if (sp != PREC_F32) {
+      if (sp != cp) {
         for (int r = 0; r < R; r++)
-          launch_field_convert(g, PREC_F32, Vj(j) + (size_t)r * n, nullptr, sp, vsb + (size_t)r * fb,
+          launch_field_convert(g, cp, (char*)Vj(j) + (size_t)r * cb, nullptr, sp, vsb + (size_t)r * fb,
                                sp == PREC_F16 ? vsn + (size_t)r * g.V : nullptr, c->stream);
         vin = vsb;
         vinn = sp == PREC_F16 ? vsn : nullptr;
       }
       mg_precondition(c, sp, Zj(j), Zjn(j), vin, vinn, mu, R);
-      const float2* zin = (const float2*)Zj(j);
-      if (sp != PREC_F32) {
+      const void* zin = Zj(j);
+      if (sp != cp) {
         for (int r = 0; r < R; r++)
           launch_field_convert(g, sp, (char*)Zj(j) + (size_t)r * fb, sp == PREC_F16 ? Zjn(j) + (size_t)r * g.V : nullptr,
-                               PREC_F32, t32 + (size_t)r * n, nullptr, c->stream);
+                               cp, t32 + (size_t)r * cb, nullptr, c->stream);
         zin = t32;
       }
-      D32(w, zin);
-      B.dots_dev(s32(V), (size_t)R * n, j + 1, s32(w), h);
-      B.maxpy_dev(s32(w), s32(V), (size_t)R * n, j + 1, h, -1.0, nullptr);
-      B.dots_dev(s32(V), (size_t)R * n, j + 1, s32(w), h2);
-      B.maxpy_dev(s32(w), s32(V), (size_t)R * n, j + 1, h2, -1.0, nr2);
+      Dcyc(w, zin);
+      B.dots_dev(sc_(V), (size_t)R * n, j + 1, sc_(w), h);
+      B.maxpy_dev(sc_(w), sc_(V), (size_t)R * n, j + 1, h, -1.0, nullptr);
+      B.dots_dev(sc_(V), (size_t)R * n, j + 1, sc_(w), h2);
+      B.maxpy_dev(sc_(w), sc_(V), (size_t)R * n, j + 1, h2, -1.0, nr2);
       launch_arnoldi_step(ad, j, h, h2, nr2, c->stream, false);
       fetch_est(j & 1);
-      if (j < m - 1) B.scale_dev(ad.scale, s32(w), s32(Vj(j + 1)));
+      if (j < m - 1) B.scale_dev(ad.scale, sc_(w), sc_(Vj(j + 1)));
       res.iters++;
       k = j + 1;
       if (j >= 1) {
@@ -543,10 +551,14 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
     // x += sum_j y_j Z_j in FP64
     double* t64 = (double*)c->scratch.get("out_t64", (size_t)R * n * 16);
     for (int j = 0; j < k; j++) {
-      for (int r = 0; r < R; r++)
-        launch_field_convert(g, sp, (char*)Zj(j) + (size_t)r * fb, sp == PREC_F16 ? Zjn(j) + (size_t)r * g.V : nullptr,
-                             PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
-      B.maxpy_dev(s64(x), s64(t64), 0, 1, y + (size_t)j * R, +1.0, nullptr);
+      const double* zj = (const double*)Zj(j);
+      if (sp != PREC_F64) {
+        for (int r = 0; r < R; r++)
+          launch_field_convert(g, sp, (char*)Zj(j) + (size_t)r * fb, sp == PREC_F16 ? Zjn(j) + (size_t)r * g.V : nullptr,
+                               PREC_F64, t64 + 2 * (size_t)r * n, nullptr, c->stream);
+        zj = t64;
+      }
+      B.maxpy_dev(s64(x), s64(zj), 0, 1, y + (size_t)j * R, +1.0, nullptr);
     }
   }
   return res;
@@ -577,7 +589,8 @@ void run_setup(ddtm_ctx* c, double mu, uint64_t seed) {
   c->tv0.ensure((size_t)nv * n * sizeof(float2));
   float2* tv = c->tv0.as<float2>();
   for (int i = 0; i < nv; i++) launch_gaussian(tv + (size_t)i * n, n, seed * 0x100000001b3ull + (uint64_t)i * (n * 2 + 17), c->stream);
-  int sp = p.smoother_prec;
+  // the setup works in the smoother precision, FP32 for an FP64 smoother
+  int sp = p.smoother_prec == PREC_F64 ? PREC_F32 : p.smoother_prec;
   size_t fb = fine_field_bytes(g, sp);
   char* bs = (char*)c->scratch.get("setup_b", (size_t)nv * fb);
   float* bsn = (float*)c->scratch.get("setup_bn", (size_t)nv * g.V * 4);

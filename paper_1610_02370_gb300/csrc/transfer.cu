@@ -15,27 +15,19 @@ __device__ __forceinline__ size_t pidx(int blk, int s, int i, int comp, int loc,
   return (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc;
 }
 
-// CTA-wide sum of two doubles, result broadcast (blockDim multiple of 32)
-__device__ __forceinline__ void cta_sum2d(double& a, double& b, double* red) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
-  __syncthreads();
-  a = b = 0;
-  for (int k = 0; k < nw; k++) { a += red[2 * k]; b += red[2 * k + 1]; }
-}
-
 // Gather the chirality-s halves of nv test vectors (FP32 fine fields, internal
-// layout, field stride 12*V) into P and orthonormalise each aggregate half by
-// modified Gram-Schmidt in index order, twice.  Each thread keeps its site's 6
-// components in FP32; the CTA-wide inner products are summed in FP64.
-// One CTA per (blk, s); thread = site loc.
+// layout, field stride 12*V) into P and orthonormalise each aggregate half in
+// index order by classical Gram-Schmidt applied twice per vector (CGS2): the
+// same QR factor with positive diagonal as modified Gram-Schmidt, up to
+// rounding, with one batched CTA reduction per pass instead of one per pair.
+// Each thread keeps its site's 6 components in FP32; the CTA-wide inner
+// products are summed over warps in FP64.  One CTA per (blk, s); thread = site.
+static const int BP_CH = 8;  // inner products reduced together
 __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv, int nv, int Vb, long V) {
-  __shared__ double red[64];
+  __shared__ double red[32][2 * BP_CH];  // per warp partial sums of one chunk
+  __shared__ float2 hco[64];             // projection coefficients <v_j, v_i>
   const int blk = blockIdx.x >> 1, s = blockIdx.x & 1;
-  const int loc = threadIdx.x;
+  const int loc = threadIdx.x, lane = loc & 31, w = loc >> 5, nw = blockDim.x >> 5;
   const bool act = loc < Vb;
   if (act)
     for (int i = 0; i < nv; i++)
@@ -43,40 +35,72 @@ __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv,
         P[pidx(blk, s, i, comp, loc, nv, Vb)] =
             tv[(size_t)i * 12 * V + ((size_t)blk * 12 + 6 * s + comp) * Vb + loc];
   __syncthreads();
-  for (int sweep = 0; sweep < 2; sweep++) {
-    for (int i = 0; i < nv; i++) {
-      float2 vi[6];
-      if (act)
-        for (int comp = 0; comp < 6; comp++) vi[comp] = P[pidx(blk, s, i, comp, loc, nv, Vb)];
-      for (int j = 0; j < i; j++) {
-        float pre = 0, pim = 0;
-        float2 vj[6];
-        if (act)
-          for (int comp = 0; comp < 6; comp++) {
-            vj[comp] = P[pidx(blk, s, j, comp, loc, nv, Vb)];
-            pre += vj[comp].x * vi[comp].x + vj[comp].y * vi[comp].y;  // <v_j, v_i>
-            pim += vj[comp].x * vi[comp].y - vj[comp].y * vi[comp].x;
+  for (int i = 0; i < nv; i++) {
+    float2 vi[6];
+#pragma unroll
+    for (int comp = 0; comp < 6; comp++) vi[comp] = act ? P[pidx(blk, s, i, comp, loc, nv, Vb)] : make_float2(0.f, 0.f);
+    for (int pass = 0; pass < 2 && i > 0; pass++) {
+      // h_j = <v_j, v_i> for all j < i, in chunks of BP_CH
+      for (int j0 = 0; j0 < i; j0 += BP_CH) {
+        float pr[BP_CH], pi[BP_CH];
+#pragma unroll
+        for (int c = 0; c < BP_CH; c++) {
+          pr[c] = pi[c] = 0.f;
+          const int j = j0 + c;
+          if (act && j < i)
+#pragma unroll
+            for (int comp = 0; comp < 6; comp++) {
+              const float2 vj = P[pidx(blk, s, j, comp, loc, nv, Vb)];
+              pr[c] += vj.x * vi[comp].x + vj.y * vi[comp].y;
+              pi[c] += vj.x * vi[comp].y - vj.y * vi[comp].x;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < BP_CH; c++) {
+          const float a = warp_sum(pr[c]), b = warp_sum(pi[c]);
+          if (lane == 0) {
+            red[w][2 * c] = a;
+            red[w][2 * c + 1] = b;
           }
-        double re = pre, im = pim;
-        cta_sum2d(re, im, red);
-        const float fre = (float)re, fim = (float)im;
-        if (act)
-          for (int comp = 0; comp < 6; comp++) {
-            vi[comp].x -= fre * vj[comp].x - fim * vj[comp].y;
-            vi[comp].y -= fre * vj[comp].y + fim * vj[comp].x;
+        }
+        __syncthreads();
+        if (loc < BP_CH && j0 + loc < i) {
+          double a = 0, b = 0;
+          for (int k = 0; k < nw; k++) {
+            a += red[k][2 * loc];
+            b += red[k][2 * loc + 1];
           }
+          hco[j0 + loc] = make_float2((float)a, (float)b);
+        }
+        __syncthreads();
       }
-      float pn = 0;
+      // v_i -= sum_j h_j v_j
       if (act)
-        for (int comp = 0; comp < 6; comp++) pn += vi[comp].x * vi[comp].x + vi[comp].y * vi[comp].y;
-      double nn = pn, dummy = 0;
-      cta_sum2d(nn, dummy, red);
-      const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
-      if (act)
-        for (int comp = 0; comp < 6; comp++)
-          P[pidx(blk, s, i, comp, loc, nv, Vb)] = make_float2(vi[comp].x * inv, vi[comp].y * inv);
-      __syncthreads();
+        for (int j = 0; j < i; j++) {
+          const float2 h = hco[j];
+#pragma unroll
+          for (int comp = 0; comp < 6; comp++) {
+            const float2 vj = P[pidx(blk, s, j, comp, loc, nv, Vb)];
+            vi[comp].x -= h.x * vj.x - h.y * vj.y;
+            vi[comp].y -= h.x * vj.y + h.y * vj.x;
+          }
+        }
+      __syncthreads();  // hco is rewritten by the next pass
     }
+    float pn = 0;
+#pragma unroll
+    for (int comp = 0; comp < 6; comp++) pn += vi[comp].x * vi[comp].x + vi[comp].y * vi[comp].y;
+    pn = warp_sum(pn);
+    if (lane == 0) red[w][0] = pn;
+    __syncthreads();
+    double nn = 0;
+    for (int k = 0; k < nw; k++) nn += red[k][0];
+    const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+    if (act)
+#pragma unroll
+      for (int comp = 0; comp < 6; comp++)
+        P[pidx(blk, s, i, comp, loc, nv, Vb)] = make_float2(vi[comp].x * inv, vi[comp].y * inv);
+    __syncthreads();  // v_i is read by the later vectors; red is reused
   }
 }
 

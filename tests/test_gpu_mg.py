@@ -189,6 +189,14 @@ def test_solve_16x16x16x32_fp16_smoother(lib):
     print("16^3x32 solves (iters, coarse iters, relres):", res)
 
 
+def test_solve_fp64_fine_level(lib):
+    """The plain FP64 method (FP64 outer FGMRES cycle and SAP smoother, FP32
+    coarse correction): FP64 relative residual 1e-10 for +mu and -mu."""
+    res = solve_case(lib, (16, 8, 8, 8), (4, 4, 4, 4), 0.2, 0.134, 1.5755, 0.01, 8, 2, False,
+                     smoother_prec=lib.PREC_F64, post_smooth=2, coarse_prec=lib.PREC_F32)
+    print("FP64 fine-level solves (iters, coarse iters, relres):", res)
+
+
 def test_setup_invariants_and_save_load(lib, tmp_path):
     dims, block = (8, 8, 8, 16), (4, 4, 4, 4)
     U = synth.gauge_field(dims, 0.2, seed=3)
