@@ -3,11 +3,14 @@ for timing and for profiling a single kernel in isolation.
 
     python -m paper_1610_02370_gb300.kernel_bench coarse --dims 48 24 24 24 --nv 24 --nrhs 12 --reps 4
     python -m paper_1610_02370_gb300.kernel_bench dslash --dims 64 32 32 32 --prec 1 --reps 10
+    python -m paper_1610_02370_gb300.kernel_bench solve --dims 64 32 32 32 --nrhs 12 --outer-iters 1
 
-``coarse`` builds the aggregation from Gaussian test vectors (no setup
-iterations) and applies the coarse operator D_c (Sec. 2.3) to a batch of
-nrhs vectors; ``dslash`` applies D(mu) (Sec. 2.1) to one field.  Each prints
-one JSON line with the median time per call (CUDA events).
+``coarse`` builds the aggregation and the Galerkin coarse operator from
+Gaussian test vectors (no setup iterations; the second build is timed per
+kernel) and applies the coarse operator D_c (Sec. 2.3) to a batch of nrhs
+vectors; ``dslash`` applies D(mu) (Sec. 2.1) to one field; ``solve`` runs the
+first outer iterations of a batched solve (every kernel of the solve phase).
+Each prints one JSON line with its times (CUDA events).
 """
 
 import argparse
@@ -44,14 +47,55 @@ def coarse(args):
         ddtm.ddtm_set_params(ctx, p)
         lat = tuple(dims)
         v = synth.gaussian_vectors((args.nv,) + lat + (4, 3), seed=5, device="cuda")
-        ddtm.ddtm_set_test_vectors(ctx, 0, v, args.nv)
+        ddtm.ddtm_set_test_vectors(ctx, 0, v, args.nv)  # warm-up build (module load, allocation)
+        ddtm.ddtm_timer_reset(ctx)
+        ddtm.ddtm_timer_enable(ctx, True)
+        ddtm.ddtm_set_test_vectors(ctx, 0, v, args.nv)  # aggregation and Galerkin, timed per kernel
+        ddtm.ddtm_timer_enable(ctx, False)
+        build = {k: round(t["ms"], 3) for k, t in ddtm.ddtm_timer_report(ctx).items()}
         del v
+        torch.cuda.empty_cache()
         cl = tuple(d // 4 for d in dims)
         x = synth.gaussian_vectors((args.nrhs,) + cl + (2 * args.nv,), seed=6, device="cuda")
         y = torch.zeros_like(x)
         ms = _events(lambda: ddtm.ddtm_apply_Dc(ctx, 1, y, x, args.nrhs, 0.01), args.reps)
         print(json.dumps({"kernel": "coarse", "dims": dims, "nv": args.nv, "nrhs": args.nrhs,
-                          "coarse_prec": args.coarse_prec, "ms_per_call": ms}))
+                          "coarse_prec": args.coarse_prec, "ms_per_call": ms, "build_ms": build}))
+    finally:
+        ddtm.ddtm_destroy(ctx)
+
+
+def solve(args):
+    """The first outer iterations of a 12-rhs solve on Gaussian test vectors (no
+    setup iterations): restriction, coarsest even-odd GMRES (tensor-core
+    passes, FP16-basis Gram-Schmidt), prolongation, SAP, FP32 D applications."""
+    dims = tuple(args.dims)
+    U = synth.gauge_field(dims, args.eps, seed=0, device="cuda")
+    ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 0)
+    try:
+        ddtm.ddtm_load_gauge(ctx, U, args.kappa, args.csw)
+        p = ddtm.ddtm_get_params(ctx)
+        p.nv[0] = args.nv
+        p.coarse_prec = args.coarse_prec
+        p.outer_restart = max(args.outer_iters, 1)
+        p.outer_max_iters = args.outer_iters
+        p.post_smooth = 2
+        ddtm.ddtm_set_params(ctx, p)
+        v = synth.gaussian_vectors((args.nv,) + tuple(dims) + (4, 3), seed=5, device="cuda")
+        ddtm.ddtm_set_test_vectors(ctx, 0, v, args.nv)
+        del v
+        torch.cuda.empty_cache()
+        b = synth.point_sources(dims, device="cuda")[: args.nrhs].contiguous()
+        x = torch.zeros_like(b)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        info, code = ddtm.ddtm_solve(ctx, x, b, args.nrhs, args.mu)
+        e1.record(st)
+        e1.synchronize()
+        print(json.dumps({"kernel": "solve", "dims": dims, "nv": args.nv, "nrhs": args.nrhs,
+                          "outer_iters": info.iters, "coarse_iters": info.coarse_iters,
+                          "max_relres": info.max_relres, "ms": e0.elapsed_time(e1)}))
     finally:
         ddtm.ddtm_destroy(ctx)
 
@@ -76,7 +120,7 @@ def dslash(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["coarse", "dslash"])
+    ap.add_argument("what", choices=["coarse", "dslash", "solve"])
     ap.add_argument("--dims", type=int, nargs=4, default=[48, 24, 24, 24])
     ap.add_argument("--eps", type=float, default=0.15)
     ap.add_argument("--kappa", type=float, default=0.137)
@@ -86,10 +130,12 @@ def main():
     ap.add_argument("--coarse-prec", type=int, default=2)
     ap.add_argument("--prec", type=int, default=1)
     ap.add_argument("--reps", type=int, default=4)
+    ap.add_argument("--mu", type=float, default=0.0015)
+    ap.add_argument("--outer-iters", type=int, default=1)
     args = ap.parse_args()
     from . import build
     build.build()
-    {"coarse": coarse, "dslash": dslash}[args.what](args)
+    {"coarse": coarse, "dslash": dslash, "solve": solve}[args.what](args)
 
 
 if __name__ == "__main__":
