@@ -56,6 +56,13 @@ void* ScratchPool::get(const std::string& name, size_t bytes) {
   return b->p;
 }
 
+size_t ScratchPool::held(const std::string& prefix) const {
+  size_t s = 0;
+  for (const auto& kv : bufs)
+    if (kv.first.compare(0, prefix.size(), prefix) == 0) s += kv.second->bytes;
+  return s;
+}
+
 // local coordinates (per direction t, x, y, z) of local index loc
 static void loc_coords(const int b[4], int loc, int c[4]) {
   int Vh = b[0] * b[1] * b[2] * b[3] / 2;

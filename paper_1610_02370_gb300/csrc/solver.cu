@@ -861,17 +861,25 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
   API_END(ctx)
 }
 
-// right-hand sides per outer batch: all of them if the FP64 basis, the stored
-// preconditioned vectors and the work fields fit in 60% of the free memory
+// Right-hand sides per outer batch: all of them when the per-rhs work fields
+// of the outer solver (FP64 input, output and residual, the cycle-precision
+// basis of outer_restart + 1 fields, the stored preconditioned fields in the
+// smoother precision, the work fields) fit in the device memory that is free
+// or already held by those same buffers (they are reused or regrown), less a
+// reserve of 10% of the device for everything else.
 static int solve_batch(ddtm_ctx* ctx, int nrhs) {
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
   const FineGeom& g = ctx->g;
-  int m = ctx->p.outer_restart;
-  size_t per = (size_t)g.V * 12 * ((m + 1) * 16 + m * store2_bytes(ctx->p.smoother_prec) + 3 * 16 + 4 * 8) +
-               (size_t)g.V * (m + 2) * 4;
-  size_t budget = (size_t)(0.6 * (double)fr);
-  int R = per > 0 ? (int)(budget / per) : nrhs;
+  const int m = ctx->p.outer_restart, sp = ctx->p.smoother_prec;
+  const size_t cyc = sp == PREC_F64 ? 16 : 8;  // bytes per complex entry of the cycle precision
+  const size_t n = (size_t)g.V * 12;
+  const size_t per = n * ((m + 1) * cyc + m * store2_bytes(sp) + 4 * 16 + 3 * cyc + 2 * store2_bytes(sp)) +
+                     (size_t)g.V * (m + 2) * sizeof(float);
+  const size_t held = ctx->scratch.held("out_") + ctx->scratch.held("solve_");
+  const size_t reserve = tot / 10;
+  const size_t avail = fr + held > reserve ? fr + held - reserve : 0;
+  int R = per > 0 ? (int)(avail / per) : nrhs;
   if (R < 1) R = 1;
   return R < nrhs ? R : nrhs;
 }
