@@ -91,20 +91,23 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc):
     return None
 
 
-def algorithmic_flops(name, Vb, b, nv):
-    """Algorithmic FP32 flops of one launch of the compute-bound setup kernels
-    (None otherwise), per aggregate times the number of aggregates."""
+def algorithmic_flops(name, V, Vb, b, nv, nmr, rhs_per_launch):
+    """Algorithmic FP32 flops of one launch of the compute-bound kernels (None
+    otherwise): Galerkin build and Gram-Schmidt per aggregate times the number
+    of aggregates; SAP half-sweep (n_MR + 1) D applications of 1920 flops per
+    site of the colour, per right-hand side."""
     n = 2 * nv
+    Nc = V // Vb
     if name == "galerkin":
         # D applied to the n columns of P on the aggregate and its faces (1920 flops per site),
         # self block: n x n entries of 6 Vb complex products; hop block k: 6 Vb / b_k products
-        per = n * Vb * 1920 + 8 * n * n * 6 * Vb + sum(2 * 8 * n * n * 6 * Vb / bb for bb in b)
-        return per
+        return Nc * (n * Vb * 1920 + 8 * n * n * 6 * Vb + sum(2 * 8 * n * n * 6 * Vb / bb for bb in b))
     if name == "build_P":
-        # two modified Gram-Schmidt passes over the nv vectors of each aggregate half (6 Vb entries)
+        # two Gram-Schmidt passes over the nv vectors of each aggregate half (6 Vb entries)
         m = 6 * Vb
-        per_half = 2 * (nv * (nv - 1) / 2 * 16 * m + nv * 8 * m)
-        return 2 * per_half
+        return Nc * 2 * 2 * (nv * (nv - 1) / 2 * 16 * m + nv * 8 * m)
+    if name.startswith("sap_half_"):
+        return rhs_per_launch * (V / 2) * (nmr + 1) * 1920
     return None
 
 
@@ -426,16 +429,21 @@ def main():
     launches = counts[dom]["launches"]
     avg_s = counts[dom]["ms"] / launches / 1000.0
     nbytes = bytes_per_launch(dom)
-    fl = algorithmic_flops(dom, Vb, MG["block"], MG["nv"])
+    def flops_per_launch(k):
+        v = counts[k]
+        return algorithmic_flops(k, V, Vb, MG["block"], MG["nv"], MG["nmr"],
+                                 v.get("units", v["launches"]) / v["launches"])
+    fl = flops_per_launch(dom)
     if fl:
         # FP32 SIMT arithmetic: 152 SMs x 128 FMA lanes x 2 flops at the sampled SM clock
         alu = 152 * 128 * 2 * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
-        per_launch = fl * Nc
+        per_launch = fl
         achieved = per_launch / avg_s / 1e12
         roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
                     "frac": achieved / alu, "traffic": None, "share": counts[dom]["ms"] / total_ms,
                     "launches_per_step": launches / args.steps, "flops_per_launch": per_launch,
-                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x sampled SM clock"}
+                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x sampled SM clock",
+                    "bytes_per_launch": nbytes}
     else:
         achieved = nbytes / avg_s / 1e9 if nbytes else None
         roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -445,9 +453,9 @@ def main():
     breakdown = {}
     for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"]):
         nb = bytes_per_launch(k)
-        fk = algorithmic_flops(k, Vb, MG["block"], MG["nv"])
+        fk = flops_per_launch(k)
         breakdown[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                        "tflops": fk * Nc / (v["ms"] / v["launches"] / 1000.0) / 1e12 if fk else None,
+                        "tflops": fk / (v["ms"] / v["launches"] / 1000.0) / 1e12 if fk else None,
                         "units_per_step": v.get("units", v["launches"]) / args.steps,
                         "share": v["ms"] / total_ms,
                         "gbs": nb / (v["ms"] / v["launches"] / 1000.0) / 1e9 if nb else None}
