@@ -21,8 +21,9 @@ void launch_gaussian(float2* out, size_t n, uint64_t key, cudaStream_t st);
 void launch_P_to_canon(const FineGeom& g, double* W, const float2* P, int nv, cudaStream_t st);
 
 // coarse.cu
+// rows_fp16: the rows of P enter the projections rounded to FP16 (for FP16 coarse storage)
 void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* Dc, const float2* P, const void* links32,
-                     const void* clover32, int nv, cudaStream_t st);
+                     const void* clover32, int nv, bool rows_fp16, cudaStream_t st);
 // Batched coarse vectors: R right-hand sides interleaved, v[(site * n + k) * R + r].
 // full-lattice vectors: y = sy*y + sres * (mode&1: self + i mu_c Gamma5_c, mode&2: hops) x
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,

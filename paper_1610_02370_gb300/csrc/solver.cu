@@ -105,7 +105,7 @@ void build_hierarchy(ddtm_ctx* c) {
   L.prec = c->p.coarse_prec;
   L.Dc.ensure((size_t)L.Nc * 9 * L.n * L.n * 8);
   launch_galerkin(g, c->faces, PREC_F32, L.Dc.p, c->P0.as<float2>(), c->links[PREC_F32].p, c->clover[PREC_F32].p, nv,
-                  c->stream);
+                  L.prec == PREC_F16, c->stream);
   if (L.prec == PREC_F16) build_coarse_images(L, c->stream);
   L.inv_valid = false;
   L.built = true;
