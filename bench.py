@@ -91,6 +91,13 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc):
     return None
 
 
+# DRAM traffic per unit from one ncu capture of the kernel as it stands (profiles/), scaled to a
+# launch of the bench workload by the units it processes; remove an entry when its kernel changes.
+NCU_TRAFFIC = {
+    "sap_half_f16": {"bytes_per_site_rhs": 1.0652e9 / (663552 / 2 * 12), "capture": "k_sap_half_24x24x24x48.md"},
+}
+
+
 def algorithmic_flops(name, V, Vb, b, nv, nmr, rhs_per_launch):
     """Algorithmic FP32 flops of one launch of the compute-bound kernels (None
     otherwise): Galerkin build and Gram-Schmidt per aggregate times the number
@@ -439,8 +446,12 @@ def main():
         alu = 152 * 128 * 2 * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
         per_launch = fl
         achieved = per_launch / avg_s / 1e12
+        tr = NCU_TRAFFIC.get(dom)
+        rpl = counts[dom].get("units", launches) / launches
+        traffic = tr["bytes_per_site_rhs"] * (V / 2) * rpl if tr else None
         roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
-                    "frac": achieved / alu, "traffic": None, "share": counts[dom]["ms"] / total_ms,
+                    "frac": achieved / alu, "traffic": traffic, "traffic_capture": tr["capture"] if tr else None,
+                    "share": counts[dom]["ms"] / total_ms,
                     "launches_per_step": launches / args.steps, "flops_per_launch": per_launch,
                     "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x sampled SM clock",
                     "bytes_per_launch": nbytes}

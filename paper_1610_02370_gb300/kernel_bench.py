@@ -4,12 +4,14 @@ for timing and for profiling a single kernel in isolation.
     python -m paper_1610_02370_gb300.kernel_bench coarse --dims 48 24 24 24 --nv 24 --nrhs 12 --reps 4
     python -m paper_1610_02370_gb300.kernel_bench dslash --dims 64 32 32 32 --prec 1 --reps 10
     python -m paper_1610_02370_gb300.kernel_bench solve --dims 64 32 32 32 --nrhs 12 --outer-iters 1
+    python -m paper_1610_02370_gb300.kernel_bench sap --dims 48 24 24 24 --nrhs 12 --cycles 2
 
 ``coarse`` builds the aggregation and the Galerkin coarse operator from
 Gaussian test vectors (no setup iterations; the second build is timed per
 kernel) and applies the coarse operator D_c (Sec. 2.3) to a batch of nrhs
 vectors; ``dslash`` applies D(mu) (Sec. 2.1) to one field; ``solve`` runs the
-first outer iterations of a batched solve (every kernel of the solve phase).
+first outer iterations of a batched solve (every kernel of the solve phase);
+``sap`` runs the SAP smoother (Sec. 2.4) on a batch of Gaussian right-hand sides.
 Each prints one JSON line with its times (CUDA events).
 """
 
@@ -93,9 +95,33 @@ def solve(args):
         info, code = ddtm.ddtm_solve(ctx, x, b, args.nrhs, args.mu)
         e1.record(st)
         e1.synchronize()
+        if code not in (ddtm.OK, ddtm.ERR_NOCONV):
+            raise ddtm.DDTMError(code, ddtm.ddtm_last_error(ctx))
         print(json.dumps({"kernel": "solve", "dims": dims, "nv": args.nv, "nrhs": args.nrhs,
                           "outer_iters": info.iters, "coarse_iters": info.coarse_iters,
                           "max_relres": info.max_relres, "ms": e0.elapsed_time(e1)}))
+    finally:
+        ddtm.ddtm_destroy(ctx)
+
+
+def sap(args):
+    """SAP smoother (Sec. 2.4) on a batch of nrhs Gaussian right-hand sides from x = 0."""
+    dims = tuple(args.dims)
+    U = synth.gauge_field(dims, args.eps, seed=0, device="cuda")
+    ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 0)
+    try:
+        ddtm.ddtm_load_gauge(ctx, U, args.kappa, args.csw)
+        b = synth.gaussian_spinor(dims, seed=1, nrhs=args.nrhs, device="cuda")
+        fb = ddtm.ddtm_field_create(ctx, args.sap_prec, args.nrhs)
+        fx = ddtm.ddtm_field_create(ctx, args.sap_prec, args.nrhs)
+        ddtm.ddtm_field_import(ctx, fb, b)
+        del b
+        torch.cuda.empty_cache()
+        ms = _events(lambda: ddtm.ddtm_sap_field(ctx, fx, fb, args.mu, args.cycles, args.nmr), args.reps)
+        print(json.dumps({"kernel": "sap", "dims": dims, "prec": args.sap_prec, "nrhs": args.nrhs, "cycles": args.cycles,
+                          "nmr": args.nmr, "ms_per_call": ms}))
+        ddtm.ddtm_field_destroy(fx)
+        ddtm.ddtm_field_destroy(fb)
     finally:
         ddtm.ddtm_destroy(ctx)
 
@@ -120,7 +146,7 @@ def dslash(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["coarse", "dslash", "solve"])
+    ap.add_argument("what", choices=["coarse", "dslash", "solve", "sap"])
     ap.add_argument("--dims", type=int, nargs=4, default=[48, 24, 24, 24])
     ap.add_argument("--eps", type=float, default=0.15)
     ap.add_argument("--kappa", type=float, default=0.137)
@@ -132,10 +158,13 @@ def main():
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--mu", type=float, default=0.0015)
     ap.add_argument("--outer-iters", type=int, default=1)
+    ap.add_argument("--sap-prec", type=int, default=2)
+    ap.add_argument("--cycles", type=int, default=2)
+    ap.add_argument("--nmr", type=int, default=3)
     args = ap.parse_args()
     from . import build
     build.build()
-    {"coarse": coarse, "dslash": dslash, "solve": solve}[args.what](args)
+    {"coarse": coarse, "dslash": dslash, "solve": solve, "sap": sap}[args.what](args)
 
 
 if __name__ == "__main__":
