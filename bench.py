@@ -118,6 +118,17 @@ def algorithmic_flops(name, V, Vb, b, nv, nmr, rhs_per_launch):
     return None
 
 
+def max_over_ranks(value, dist, device):
+    """Largest per-rank value over the job (the slowest replica sets the step
+    time); ``dist`` is torch.distributed or None for one process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,10 +392,7 @@ def main():
     counts = ddtm.ddtm_timer_report(ctx)
     ms = ev0.elapsed_time(ev1)
     t_step = ms / 1000.0 / args.steps
-    if dist is not None:
-        t = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(t_step, dist, "cuda")
     value = t_step / world  # whole job: world propagators per step
 
     # residual check of the last solve with the library's FP64 operator
@@ -487,11 +495,7 @@ def main():
             info, code = ddtm.ddtm_solve(ctx, xh, bh, NRHS, mu)
             barrier()
             ts.append(time.perf_counter() - t0)
-        te = max(ts) if ts else float("nan")
-        if dist is not None:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(max(ts) if ts else float("nan"), dist, "cuda")
         e2e = {"value": te / world, "unit": UNIT, "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
                "d2h_bytes_per_step": int(xh.numel() * 16)}
 
