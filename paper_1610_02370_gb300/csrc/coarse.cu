@@ -20,10 +20,8 @@ namespace ddtm {
 
 template <typename DS> __device__ __forceinline__ cplx<float> ldD(const DS* p);
 template <> __device__ __forceinline__ cplx<float> ldD<float2>(const float2* p) { return ld(p); }
-template <> __device__ __forceinline__ cplx<float> ldD<__half2>(const __half2* p) { return ld(p); }
 template <typename DS> __device__ __forceinline__ void stD(DS* p, cplx<float> v);
 template <> __device__ __forceinline__ void stD<float2>(float2* p, cplx<float> v) { st(p, v); }
-template <> __device__ __forceinline__ void stD<__half2>(__half2* p, cplx<float> v) { st(p, v); }
 
 __device__ __forceinline__ size_t pix(int blk, int s, int i, int comp, int loc, int nv, int Vb) {
   return (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc;
@@ -313,19 +311,12 @@ __device__ __forceinline__ void load_rc(const cplx<float>* p, cplx<float> v[RC])
 }
 
 // Two consecutive rows (r, r+1) of column k of a column-major block: one
-// 16-byte (FP32) or 8-byte (FP16) load.
+// 16-byte load.
 template <typename DS> __device__ __forceinline__ void ld_rows2(const DS* p, cplx<float>& a0, cplx<float>& a1);
 template <> __device__ __forceinline__ void ld_rows2<float2>(const float2* p, cplx<float>& a0, cplx<float>& a1) {
   float4 v = __ldg(reinterpret_cast<const float4*>(p));
   a0 = cplx<float>(v.x, v.y);
   a1 = cplx<float>(v.z, v.w);
-}
-template <> __device__ __forceinline__ void ld_rows2<__half2>(const __half2* p, cplx<float>& a0, cplx<float>& a1) {
-  float2 raw = __ldg(reinterpret_cast<const float2*>(p));
-  __half2 h0 = *reinterpret_cast<__half2*>(&raw.x), h1 = *reinterpret_cast<__half2*>(&raw.y);
-  float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-  a0 = cplx<float>(f0.x, f0.y);
-  a1 = cplx<float>(f1.x, f1.y);
 }
 
 // acc{0,1}[c] += A[r0 + {0,1}][k] v[k][c] for a column-major n x n block whose
