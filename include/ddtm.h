@@ -239,8 +239,11 @@ int ddtm_load_setup(ddtm_ctx* ctx, const char* path);
  * on its stream.  Timers are process-wide (shared by all contexts). */
 int ddtm_timer_enable(ddtm_ctx* ctx, int on);
 int ddtm_timer_reset(ddtm_ctx* ctx);
-/* Write a JSON object {"kernel": {"launches": n, "ms": total}, ...} into buf
- * (NUL-terminated, truncated to len); synchronises the recorded events. */
+/* Write a JSON object {"_kernel_launches": k, "name": {"launches": n, "ms": total, "units": u,
+ * "bytes": b}, ...} into buf (NUL-terminated, truncated to len); synchronises the recorded events.
+ * k counts every kernel the library launched since the last reset (timed or not); per name, n
+ * counts timed launch scopes, u their work units (right-hand sides or vectors) and b their
+ * algorithmic bytes where the library states them (0 otherwise). */
 int ddtm_timer_report(ddtm_ctx* ctx, char* buf, int len);
 
 #ifdef __cplusplus

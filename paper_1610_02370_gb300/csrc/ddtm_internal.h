@@ -22,8 +22,11 @@ struct Error : std::runtime_error {
 };
 
 void cuda_check(cudaError_t e, const char* what);
+// after every kernel launch: counts the launch (kernel_launches()) and checks it
+void cuda_check_launch(const char* what);
+long kernel_launches();
 #define CK(x) ::ddtm::cuda_check((x), #x)
-#define CKL(what) ::ddtm::cuda_check(cudaGetLastError(), what)
+#define CKL(what) ::ddtm::cuda_check_launch(what)
 
 // Owned device allocation.
 struct DevBuf {

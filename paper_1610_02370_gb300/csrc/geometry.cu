@@ -7,11 +7,20 @@
 // block extent is even, block origins have even parity, so the local parity is
 // the global parity (t + x + y + z) mod 2, and each x-row of a block holds
 // alternating parities, which makes (parity, lexloc >> 1) a bijection.
+#include <atomic>
+
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "timer.h"
 
 namespace ddtm {
+
+static std::atomic<long> g_kernel_launches{0};
+long kernel_launches() { return g_kernel_launches.load(); }
+void cuda_check_launch(const char* what) {
+  g_kernel_launches.fetch_add(1);
+  cuda_check(cudaGetLastError(), what);
+}
 
 void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {

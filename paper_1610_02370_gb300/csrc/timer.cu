@@ -26,6 +26,7 @@ struct State {
   cudaEvent_t cur_a = nullptr;
   long cur_units = 0;
   double cur_bytes = 0;
+  long launch_base = 0;
 };
 State& S() {
   static State s;
@@ -68,11 +69,13 @@ void timer_enable(bool on) {
 void timer_reset() {
   flush();
   S().acc.clear();
+  S().launch_base = kernel_launches();
 }
 std::string timer_report_json() {
   flush();
-  std::string out = "{";
-  bool first = true;
+  // "_kernel_launches": every kernel launched by the library since the last reset
+  std::string out = "{\"_kernel_launches\": " + std::to_string(kernel_launches() - S().launch_base);
+  bool first = false;
   for (auto& kv : S().acc) {
     char buf[256];
     snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %ld, \"ms\": %.6f, \"units\": %ld, \"bytes\": %.0f}",

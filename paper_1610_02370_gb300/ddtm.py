@@ -281,9 +281,20 @@ def ddtm_timer_reset(ctx):
     _check(ctx, _lib.ddtm_timer_reset(ctx))
 
 
-def ddtm_timer_report(ctx):
-    """Per-kernel {name: {"launches": n, "ms": total}} since the last reset."""
+def _timer_json(ctx):
     import json
     buf = ctypes.create_string_buffer(1 << 16)
     _check(ctx, _lib.ddtm_timer_report(ctx, buf, len(buf)))
     return json.loads(buf.value.decode())
+
+
+def ddtm_timer_report(ctx):
+    """Per-kernel {name: {"launches": n, "ms": total, "units": u, "bytes": b}} since the last reset."""
+    d = _timer_json(ctx)
+    d.pop("_kernel_launches", None)
+    return d
+
+
+def ddtm_timer_kernel_launches(ctx):
+    """Kernels the library launched since the last timer reset (timed or not)."""
+    return int(_timer_json(ctx).get("_kernel_launches", 0))
