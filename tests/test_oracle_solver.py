@@ -13,7 +13,9 @@ Krylov space (checked against library least squares), even-odd GMRES solves
 the coarse system and its retrieval makes the even rows exact.
 Multigrid (Sec. 2.2): the preconditioner's error propagation is
 E_SAP^k (I - P D_c^-1 R D); the two-level solve reaches 1e-10 and the dense
-solution, for +mu and -mu with one setup.
+solution, for +mu and -mu with one setup.  Three levels (the K-cycle of
+Sec. 2.2 / 2.5 with FGMRES on the intermediate level): the level-2 operator is
+the dense Galerkin product of the level-1 operator, and the solve reaches 1e-10.
 """
 
 import numpy as np
@@ -360,3 +362,51 @@ def test_two_level_solve_config_4x4x4x4(fine, fine_dense):
     W = h.W[0]
     g = blocks.block_sum(np.conj(W[1, 3]) * W[1, 3], fine.lat, B2)
     assert np.max(np.abs(g - 1)) < 1e-13
+
+
+@pytest.fixture(scope="module")
+def three_level():
+    """8^4 fine lattice, 2^4 aggregates on both levels: level 1 is 4^4 x 8 dofs, level 2 is 2^4 x 8."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.3, seed=0).numpy()
+    op = FineOperator(U, 0.125, 1.0)
+    mu = 0.01
+    p = mg.Params(nlevels=3, n_setup=2, nv=[4, 4], bdims=[B2, B2], post_smooth=2, nmr=3)
+    cl = blocks.coarse_lat(op.lat, B2)
+    tv0 = [synth.gaussian_vectors((4,) + op.lat + op.dof, seed=31).numpy(),
+           synth.gaussian_vectors((4,) + cl + (8,), seed=32).numpy()]
+    h = mg.setup(op, p, mu, tv0)
+    return op, h, mu
+
+
+@pytest.mark.slow
+def test_three_level_galerkin_is_dense_product(three_level):
+    """The level-2 operator equals P_1^dagger D_1 P_1 (+ i delta mu Gamma5 on the coarsest level),
+    with D_1 itself a Galerkin operator: the recursion of Sec. 2.3 applied twice."""
+    op, h, mu = three_level
+    D1, D2 = h.ops[1], h.ops[2]
+    W1 = h.W[1]
+    mu2 = h.mu_at(2, mu)
+    D1m = dense(lambda v: D1.apply(v, mu2), D1.lat + D1.dof)
+    n1, n2 = int(np.prod(D1.lat + D1.dof)), int(np.prod(D2.lat + D2.dof))
+    Pm = np.zeros((n1, n2), dtype=complex)
+    for k in range(n2):
+        e = np.zeros(n2, dtype=complex)
+        e[k] = 1
+        Pm[:, k] = aggregation.prolong(W1, e.reshape(D2.lat + D2.dof), D1.lat, B2).ravel()
+    assert np.allclose(Pm.conj().T @ Pm, np.eye(n2), atol=1e-12)
+    want = Pm.conj().T @ D1m @ Pm
+    got = dense(lambda v: D2.apply(v, mu2), D2.lat + D2.dof)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+@pytest.mark.slow
+def test_three_level_solve(three_level):
+    """Outer FGMRES with the K-cycle (FGMRES(5) on level 1, even-odd GMRES on level 2) reaches
+    the FP64 relative residual 1e-10 for +mu and -mu with one setup."""
+    op, h, mu = three_level
+    b = synth.gaussian_spinor((8, 8, 8, 8), seed=1).numpy()
+    for m in (mu, -mu):
+        x, info = mg.solve(h, b, m)
+        assert info['converged']
+        assert dirac.norm(b - op.apply(x, m)) <= 1e-10 * dirac.norm(b)
