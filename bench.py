@@ -139,6 +139,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--oracle-units", default=None, help=argparse.SUPPRESS)  # child process of the CPU baseline
     return ap.parse_args()
 
 
@@ -248,6 +249,21 @@ def oracle_unit_times(wl, sample_dims=(16, 8, 8, 8)):
     return out
 
 
+ONE_THREAD = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def oracle_unit_times_one_core(workload):
+    """oracle_unit_times in a child process whose BLAS / OpenMP pools are
+    limited to one thread, so the baseline runs on exactly one host core."""
+    env = dict(os.environ, **ONE_THREAD)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-units", workload],
+                       capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def oracle_estimate(unit, counts, V, Nc):
     """Oracle seconds for the GPU step's work: every kernel family's work units
     (right-hand sides or vectors processed, summed over its launches) times the
@@ -278,9 +294,10 @@ def oracle_estimate(unit, counts, V, Nc):
 # counts change.
 REFERENCE_COUNTS = {
     "dslash_f32": {"launches": 324, "units": 324}, "dslash_f64": {"launches": 24, "units": 24},
-    "sap_half_f16": {"launches": 348, "units": 0}, "build_P": {"launches": 6, "units": 144},
-    "galerkin": {"launches": 6, "units": 6}, "restrict_f16": {"launches": 86, "units": 0},
-    "prolong_f16": {"launches": 86, "units": 0}, "coarse_tc_hop_even": {"launches": 14788, "units": 0},
+    "sap_half_f16": {"launches": 132, "units": 1872}, "build_P": {"launches": 6, "units": 144},
+    "galerkin": {"launches": 6, "units": 6}, "restrict_f16": {"launches": 32, "units": 444},
+    "prolong_f16": {"launches": 32, "units": 444}, "coarse_tc_hop_even": {"launches": 5340, "units": 71196},
+    "coarse_even_f32": {"launches": 64, "units": 888},
 }
 
 
@@ -297,7 +314,7 @@ def reference_arm(args):
     counts = json.loads(os.environ.get("DDTM_REFERENCE_COUNTS", "null")) or REFERENCE_COUNTS
     vals = []
     for i in range(args.warmup + args.steps):
-        unit = oracle_unit_times(wl)
+        unit = oracle_unit_times_one_core(args.workload)
         est, _ = oracle_estimate(unit, counts, V, Nc)
         if i >= args.warmup:
             vals.append(est)
@@ -318,6 +335,9 @@ def reference_arm(args):
 # ---- our arm ------------------------------------------------------------------------------------
 def main():
     args = parse_args()
+    if args.oracle_units:
+        print(json.dumps(oracle_unit_times(WORKLOADS[args.oracle_units])))
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -538,7 +558,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        unit = oracle_unit_times(wl)
+        unit = oracle_unit_times_one_core(args.workload)
         per_step_counts = {k: {"launches": v["launches"] / args.steps, "units": v.get("units", v["launches"]) / args.steps}
                            for k, v in counts.items()}
         est, _ = oracle_estimate(unit, per_step_counts, V, Nc)
