@@ -179,7 +179,8 @@ int ddtm_field_import(ddtm_ctx* ctx, ddtm_field* f, const double* x, int loc);
 int ddtm_field_export(ddtm_ctx* ctx, const ddtm_field* f, double* x, int loc);
 /* y = D(mu) x on fields of equal precision and nrhs (Sec. 2.1). */
 int ddtm_apply_D_field(ddtm_ctx* ctx, ddtm_field* y, const ddtm_field* x, double mu);
-/* x = SAP(b) as in ddtm_sap, on fields of equal precision (F32 or F16) and nrhs. */
+/* x = SAP(b) as in ddtm_sap, on fields of equal precision (F64, F32 or F16) and nrhs; all
+ * right-hand sides go through one launch per half-sweep. */
 int ddtm_sap_field(ddtm_ctx* ctx, ddtm_field* x, const ddtm_field* b, double mu, int ncycles, int nmr);
 
 /* ---- aggregation and coarse levels (Sec. 2.3) ------------------------------ */
@@ -208,21 +209,29 @@ int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* c, int nrhs,
 
 /* y = D_level(mu) x on coarse vectors, D_c(mu) = P^+ D P + i mu Gamma5_c
  * (Sec. 2.3); level >= 1.  mu is used as given (pass delta*mu for the
- * shifted coarsest operator). */
+ * shifted coarsest operator).  All nrhs vectors go through one batched
+ * stencil pass: FP32 blocks on the SIMT cores (coarse_prec F32), or FP16
+ * operand images on the tensor cores with FP32 accumulation (coarse_prec
+ * F16; DDTM_ERR_TIMEOUT if a pipeline wait of that kernel gave up). */
 int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs, double mu, int loc);
 
 /* Even-odd preconditioned GMRES on the coarsest level (Sec. 2.5) for
  * D_c(mu_c) x = b with mu_c as given; restart length, restarts and tolerance
- * from the parameters.  *iters receives the iteration count.  Returns
- * DDTM_ERR_NOCONV if the tolerance was not reached. */
+ * from the parameters (with coarse_prec F16 the Schur complement runs on the
+ * tensor cores and the Krylov basis is stored in FP16).  *iters receives the
+ * iteration count.  Returns DDTM_ERR_NOCONV if the tolerance was not reached. */
 int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, int loc, int* iters);
 
 /* ---- solve (Sec. 2.2, 2.5) ---------------------------------------------------- */
 
 /* Solve D(mu) x = b for nrhs right-hand sides to params.outer_tol (relative,
  * FP64 residual) with flexible GMRES preconditioned by the K-cycle multigrid;
- * mu may be +mu or -mu with one setup (Sec. 3.1).  info may be NULL.
- * DDTM_ERR_NOCONV (info still filled) if outer_max_iters is exhausted. */
+ * mu may be +mu or -mu with one setup (Sec. 3.1).  The right-hand sides are
+ * solved in lockstep as one batch (every stencil, smoother and coarse-solve
+ * launch covers all of them) unless their outer-solver fields do not fit in
+ * the device memory, in which case they are split into equal batches.  info
+ * may be NULL.  DDTM_ERR_NOCONV (info still filled) if outer_max_iters is
+ * exhausted; DDTM_ERR_TIMEOUT if a tensor-core pipeline wait gave up. */
 int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int loc,
                ddtm_solve_info* info);
 
