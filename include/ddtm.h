@@ -229,7 +229,7 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
  * mu may be +mu or -mu with one setup (Sec. 3.1).  The right-hand sides are
  * solved in lockstep as one batch (every stencil, smoother and coarse-solve
  * launch covers all of them) unless their outer-solver fields do not fit in
- * the device memory, in which case they are split into equal batches.  info
+ * the device memory, in which case they go in batches of the largest size that fits.  info
  * may be NULL.  DDTM_ERR_NOCONV (info still filled) if outer_max_iters is
  * exhausted; DDTM_ERR_TIMEOUT if a tensor-core pipeline wait gave up. */
 int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int loc,
