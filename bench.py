@@ -353,8 +353,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    # one process builds (in-tree objects and library are shared by the ranks of a node)
     from paper_1610_02370_gb300 import build as _build
-    _build.build()
+    if local == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
     from paper_1610_02370_gb300 import ddtm, synth
 
     wl = WORKLOADS[args.workload]
