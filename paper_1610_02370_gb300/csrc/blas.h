@@ -4,9 +4,12 @@
 // interleaved (element (e, r) at e * R + r: coarse vectors) or separate
 // (element (e, r) at r * n + e: fine fields).  Type tags: 0 = double2 (FP64
 // complex), 1 = float2 (FP32 complex), 2 = __half2 (FP16 complex storage,
-// FP32 arithmetic; paired with FP32 sets only).  A basis of nvec sets lies at V + j*ldv
-// (ldv in complex elements).  Every inner product accumulates in FP64 and is
-// reduced in a fixed order (deterministic).  Results that come back to the
+// FP32 arithmetic; paired with FP32 sets only).  A basis of nvec sets lies at
+// V + j*ldv (ldv in complex elements).  Inner products sum per thread in the
+// operands' arithmetic precision (FP32 for FP32 / FP16 sets, FP64 otherwise)
+// and in FP64 across threads and CTAs, in a fixed order (deterministic).
+// Interleaved FP32 sets with an even number of right-hand sides use kernels
+// that read 16-byte pairs of right-hand sides.  Results that come back to the
 // host synchronise the stream; coefficients travel through a pinned ring of
 // buffers guarded by events, so no call blocks on a copy.
 #pragma once
