@@ -1,6 +1,6 @@
 // Vector kernels for the Krylov solvers (Sec. 2.5), batched over right-hand
 // sides: inner products (per-thread sums in the arithmetic precision of the
-// operands, FP64 across threads and CTAs, in a fixed order), Gram-Schmidt
+// operands, FP64 across CTAs, in a fixed order), Gram-Schmidt
 // multi-dots and multi-axpys (fused with the norms of the result), per-rhs
 // scalings, and precision conversion of fine fields.
 // Layouts and type tags are described in blas.h.

@@ -6,8 +6,9 @@
 // complex), 1 = float2 (FP32 complex), 2 = __half2 (FP16 complex storage,
 // FP32 arithmetic; paired with FP32 sets only).  A basis of nvec sets lies at
 // V + j*ldv (ldv in complex elements).  Inner products sum per thread in the
-// operands' arithmetic precision (FP32 for FP32 / FP16 sets, FP64 otherwise)
-// and in FP64 across threads and CTAs, in a fixed order (deterministic).
+// operands' arithmetic precision (FP32 for FP32 / FP16 sets, FP64 otherwise),
+// within a CTA in FP64 (generic kernels) or FP32 (pair kernels), and across
+// CTAs in FP64, always in a fixed order (deterministic).
 // Interleaved FP32 sets with an even number of right-hand sides use kernels
 // that read 16-byte pairs of right-hand sides.  Results that come back to the
 // host synchronise the stream; coefficients travel through a pinned ring of
