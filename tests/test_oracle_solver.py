@@ -1,7 +1,8 @@
 """Pins of the oracle's SAP, aggregation, Galerkin, Krylov and multigrid code.
 
 SAP (Sec. 2.4): with the block MR run to convergence, one cycle equals the
-product of dense block inverses applied red then black; MR steps satisfy their
+product of dense block inverses applied red then black (on the fine operator,
+and on a coarse operator as the smoother of an intermediate level); MR steps satisfy their
 defining orthogonality; on a block-diagonal operator one cycle solves exactly.
 Aggregation (Sec. 2.3): P^dagger P = I, Gamma5 P = P Gamma5_c, the test vectors
 lie in range(P), P equals the Q factor of a library QR per aggregate half.
@@ -95,6 +96,41 @@ def test_sap_converged_mr_equals_dense_block_inverses(fine, fine_dense, eo):
     E = (np.eye(len(bv)) - Bb @ Dm) @ (np.eye(len(bv)) - Br @ Dm)
     want = xs - E @ (E @ xs)
     got2 = sap.sap(fine, b, mu, B2, ncycles=2, nmr=120, eo=eo).ravel()
+    assert np.linalg.norm(got2 - want) < 1e-10 * np.linalg.norm(want)
+
+
+def random_coarse_operator(lat, nv, seed):
+    """A coarse operator with the nearest-neighbour block structure of Sec. 2.3 and random
+    complex blocks (self blocks shifted to be well conditioned)."""
+    rng = np.random.default_rng(seed)
+    n = 2 * nv
+    shape = (9,) + lat + (n, n)
+    bl = 0.12 * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    bl[0] += 1.5 * np.eye(n)
+    return CoarseOperator(bl, nv)
+
+
+@pytest.mark.parametrize("eo", [True, False])
+def test_sap_on_coarse_operator_equals_dense_block_inverses(eo):
+    """The smoother of an intermediate level (three levels): SAP on a coarse operator with 2^4
+    blocks of a 4^4 coarse lattice, MR run to convergence, equals red-then-black dense block
+    inverses, one and two cycles (its error propagator (I - B_bb D)(I - B_rr D))."""
+    cop = random_coarse_operator((4, 4, 4, 4), 2, seed=3)
+    mu = 0.05
+    Dm = dense(lambda v: cop.apply(v, mu), cop.lat + cop.dof)
+    sets = block_index_sets(cop, B2)
+    Br, Bb = block_inverse_dense(Dm, sets, 0), block_inverse_dense(Dm, sets, 1)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(cop.lat + cop.dof) + 1j * rng.standard_normal(cop.lat + cop.dof)
+    bv = b.ravel()
+    x1 = Br @ bv
+    x2 = x1 + Bb @ (bv - Dm @ x1)
+    got = sap.sap(cop, b, mu, B2, ncycles=1, nmr=120, eo=eo).ravel()
+    assert np.linalg.norm(got - x2) < 1e-10 * np.linalg.norm(x2)
+    xs = np.linalg.solve(Dm, bv)
+    E = (np.eye(len(bv)) - Bb @ Dm) @ (np.eye(len(bv)) - Br @ Dm)
+    want = xs - E @ (E @ xs)
+    got2 = sap.sap(cop, b, mu, B2, ncycles=2, nmr=120, eo=eo).ravel()
     assert np.linalg.norm(got2 - want) < 1e-10 * np.linalg.norm(want)
 
 
