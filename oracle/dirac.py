@@ -15,7 +15,11 @@ written from Sec. 2.1 of arXiv:1610.02370:
 * D(mu) = D_W + i mu Gamma5 (Sec. 2.1, flavour-twist display); the mass is
   m = 1/(2 kappa) - 4 and mu enters as printed, without a 2-kappa factor.
 * Boundary conditions (unstated in the paper): periodic, optionally
-  antiperiodic in t for the fermion hops (never for the gauge links).
+  antiperiodic in t for the fermion hops (never for the gauge links), and
+  optionally twisted (a library feature the paper lists in its appendix):
+  psi(x + L_mu mu_hat) = exp(i theta_mu) psi(x), i.e. a hop that wraps
+  forward in direction mu reads exp(i theta_mu) psi, one that wraps backward
+  exp(-i theta_mu) psi.
 """
 
 import numpy as np
@@ -58,15 +62,22 @@ def shift(field, mu, sign):
     return np.roll(field, -sign, axis=AXIS[mu])
 
 
-def shift_fermion(psi, mu, sign, bc_t=0):
-    """Fermion field at x + sign*mu_hat; bc_t = 1 puts a -1 on hops that wrap in t."""
+def shift_fermion(psi, mu, sign, bc_t=0, theta=None):
+    """Fermion field at x + sign*mu_hat; bc_t = 1 puts a -1 on hops that wrap in t; theta
+    (four angles, or None) multiplies hops that wrap forward in mu by exp(i theta_mu) and
+    hops that wrap backward by exp(-i theta_mu)."""
     out = shift(psi, mu, sign)
+    f = 1.0 + 0j
     if mu == 0 and bc_t == 1:
+        f = -f
+    if theta is not None and theta[mu] != 0.0:
+        f = f * np.exp(1j * sign * theta[mu])
+    if f != 1.0:
         out = out.copy()
-        if sign > 0:
-            out[-1] *= -1.0  # x0 = T-1 reads psi at x0 = 0 across the boundary
-        else:
-            out[0] *= -1.0   # x0 = 0 reads psi at x0 = T-1 across the boundary
+        edge = [slice(None)] * out.ndim
+        # forward: x_mu = L-1 reads psi at x_mu = 0; backward: x_mu = 0 reads x_mu = L-1
+        edge[AXIS[mu]] = -1 if sign > 0 else 0
+        out[tuple(edge)] *= f
     return out
 
 
@@ -138,7 +149,7 @@ def colour_mul(U, psi):
     return np.matmul(psi, np.swapaxes(U, -1, -2))
 
 
-def apply_hopping(U, psi, bc_t=0, mask_from=None):
+def apply_hopping(U, psi, bc_t=0, mask_from=None, theta=None):
     """Hopping part of D_W (Sec. 2.1):
 
     -1/2 sum_mu [(I - gamma_mu) x U_mu(x)] psi(x+mu) + [(I + gamma_mu) x U_mu(x-mu)^dagger] psi(x-mu).
@@ -148,24 +159,24 @@ def apply_hopping(U, psi, bc_t=0, mask_from=None):
     out = np.zeros_like(psi)
     for mu in range(4):
         Um = _link(U, mu)
-        fwd = shift_fermion(psi, mu, +1, bc_t)
+        fwd = shift_fermion(psi, mu, +1, bc_t, theta)
         # U_mu(x) acts on colour, (I - gamma_mu) on spin
         out -= 0.5 * np.matmul(i4 - g[mu], colour_mul(Um, fwd))
-        bwd = shift_fermion(psi, mu, -1, bc_t)
+        bwd = shift_fermion(psi, mu, -1, bc_t, theta)
         Ub = dagger(shift(Um, mu, -1))  # U_mu(x - mu)^dagger
         out -= 0.5 * np.matmul(i4 + g[mu], colour_mul(Ub, bwd))
     return out
 
 
-def apply_D(U, S, psi, mu=0.0, bc_t=0):
+def apply_D(U, S, psi, mu=0.0, bc_t=0, theta=None):
     """D(mu) psi = S psi + hopping(psi) + i mu Gamma5 psi.
 
     ``S`` is the site term from :func:`site_term`; ``psi`` is (T,Z,Y,X,4,3) or has
     a leading right-hand-side axis.
     """
     if psi.ndim == 7:
-        return np.stack([apply_D(U, S, p, mu, bc_t) for p in psi])
-    out = apply_site(S, psi) + apply_hopping(U, psi, bc_t)
+        return np.stack([apply_D(U, S, p, mu, bc_t, theta) for p in psi])
+    out = apply_site(S, psi) + apply_hopping(U, psi, bc_t, theta=theta)
     if mu != 0.0:
         out += apply_twist(psi, mu)
     return out

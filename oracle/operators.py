@@ -20,8 +20,9 @@ from . import dirac
 class FineOperator:
     """D(mu) = D_W + i mu Gamma5 on the fine lattice (Sec. 2.1)."""
 
-    def __init__(self, U, kappa, c_sw, bc_t=0):
+    def __init__(self, U, kappa, c_sw, bc_t=0, theta=None):
         self.U = U
+        self.theta = theta  # twisted boundary angles per direction mu (None: none)
         self.S = dirac.site_term(U, kappa, c_sw)
         self.lat = U.shape[:4]
         self.dof = (4, 3)
@@ -30,7 +31,7 @@ class FineOperator:
         self._g5_12 = np.kron(np.diag(self._g5).real, np.ones(3))  # gamma5 x I_3 diagonal
 
     def apply(self, psi, mu):
-        return dirac.apply_D(self.U, self.S, psi, mu, self.bc_t)
+        return dirac.apply_D(self.U, self.S, psi, mu, self.bc_t, self.theta)
 
     def site(self, psi, mu):
         out = dirac.apply_site(self.S, psi)
@@ -52,7 +53,7 @@ class FineOperator:
         return np.matmul(self._inv, psi.reshape(lat + (12, 1))).reshape(psi.shape)
 
     def hop(self, psi):
-        return dirac.apply_hopping(self.U, psi, self.bc_t)
+        return dirac.apply_hopping(self.U, psi, self.bc_t, theta=self.theta)
 
     def hop_dir(self, psi, d, sign):
         """One hopping direction of Sec. 2.1: sign=+1 gives -1/2 (I-g_d) U_d(x) psi(x+d),
@@ -60,9 +61,9 @@ class FineOperator:
         U = self.U[..., d, :, :]
         i4 = np.eye(4)
         if sign > 0:
-            nb = dirac.shift_fermion(psi, d, +1, self.bc_t)
+            nb = dirac.shift_fermion(psi, d, +1, self.bc_t, self.theta)
             return -0.5 * np.matmul(i4 - self._g[d], dirac.colour_mul(U, nb))
-        nb = dirac.shift_fermion(psi, d, -1, self.bc_t)
+        nb = dirac.shift_fermion(psi, d, -1, self.bc_t, self.theta)
         Ub = dirac.dagger(dirac.shift(U, d, -1))
         return -0.5 * np.matmul(i4 + self._g[d], dirac.colour_mul(Ub, nb))
 

@@ -2,7 +2,8 @@
 
 Each test fixes a property that a plausible slip in the oracle would break:
 * free-field plane waves (hopping signs, (1 -/+ gamma) placement, mass term,
-  twist, boundary conditions, axis-to-direction mapping);
+  twist, boundary conditions including twisted ones, axis-to-direction mapping);
+* twisted boundaries = a U(1) phase on the links crossing the boundary;
 * constant non-trivial links (U versus U^dagger and U versus U^T in the hops);
 * constant abelian field strength (clover leaves, their orientation and the
   c_sw/32 normalisation);
@@ -74,6 +75,59 @@ def test_free_field_plane_waves(bc_t):
         got = dirac.apply_D(U, S, psi, mu, bc_t)
         want = plane_wave(DIMS, p, free_symbol(p, m, mu) @ chi, col)
         assert np.max(np.abs(got - want)) < 1e-13
+
+
+@pytest.mark.parametrize("bc_t", [0, 1])
+def test_free_field_plane_waves_twisted_boundaries(bc_t):
+    """Twisted boundary conditions psi(x + L_mu) = exp(i theta_mu) psi(x): the free plane waves
+    have momenta p_mu = (2 pi n_mu + theta_mu) / L_mu (plus pi / L_t with antiperiodic t) and
+    the same symbol as without twist."""
+    rng = np.random.default_rng(13)
+    kappa, csw, mu = 0.13, 1.7, 0.23
+    m = 1 / (2 * kappa) - 4
+    theta = [0.7, -1.3, 2.1, 0.4]
+    U = synth.unit_gauge(DIMS).numpy()
+    S = dirac.site_term(U, kappa, csw)
+    for _ in range(6):
+        n = [rng.integers(0, DIMS[a]) for a in range(4)]
+        p = [(2 * np.pi * n[a] + theta[a]) / DIMS[a] for a in range(4)]
+        if bc_t == 1:
+            p[0] += np.pi / DIMS[0]
+        chi = rng.normal(size=4) + 1j * rng.normal(size=4)
+        col = rng.normal(size=3) + 1j * rng.normal(size=3)
+        psi = plane_wave(DIMS, p, chi, col)
+        got = dirac.apply_D(U, S, psi, mu, bc_t, theta)
+        want = plane_wave(DIMS, p, free_symbol(p, m, mu) @ chi, col)
+        assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_twisted_boundaries_equal_boundary_link_phases():
+    """A twist angle theta_mu on the fermion hops that wrap is the same operator as the periodic
+    one on links U_mu(x) multiplied by exp(i theta_mu) where x_mu = L_mu - 1 (a U(1) factor on the
+    links crossing the boundary: every closed loop, so the clover term, is unchanged); and
+    Gamma5-hermiticity survives the twist."""
+    dims = (4, 2, 4, 2)
+    lat = lat_of(dims)
+    U = synth.gauge_field(dims, 0.4, seed=7).numpy()
+    kappa, csw, mu = 0.125, 1.3, 0.07
+    theta = [0.9, -0.4, 1.7, 2.5]
+    Uph = U.copy()
+    for m_ in range(4):
+        edge = [slice(None)] * 4
+        edge[dirac.AXIS[m_]] = -1
+        Uph[tuple(edge) + (m_,)] *= np.exp(1j * theta[m_])
+    S = dirac.site_term(U, kappa, csw)
+    assert np.max(np.abs(dirac.site_term(Uph, kappa, csw) - S)) < 1e-13
+    psi = synth.gaussian_spinor(dims, seed=8).numpy()
+    got = dirac.apply_D(U, S, psi, mu, 0, theta)
+    want = dirac.apply_D(Uph, S, psi, mu, 0)
+    assert np.max(np.abs(got - want)) < 1e-13
+    chi = synth.gaussian_spinor(dims, seed=9).numpy()
+    g5 = lambda v: dirac.apply_Gamma5(v)
+    lhs = np.vdot(chi, g5(dirac.apply_D(U, S, g5(psi), mu, 0, theta)))
+    rhs = np.vdot(dirac.apply_D(U, S, chi, -mu, 0, theta), psi)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    assert lat == psi.shape[:4]
 
 
 def test_free_field_spectrum_singular_values():
