@@ -53,6 +53,25 @@ def galerkin(op, W, bdims):
     return out
 
 
+def projected_pweight(op, W, bdims):
+    """Q_A = P_A^dagger S P_A per aggregate: the parity weight S of op's level (+1 on even,
+    -1 on odd fine sites; already projected on coarse levels) in the coarse basis, so that the
+    Galerkin product of a different twist on even and odd sites, i Gamma5 (mbar + d S), is
+    i mbar Gamma5_c + i d Q Gamma5_c."""
+    lat = op.lat
+    nv = W.shape[1]
+    n = 2 * nv
+    clat = blocks.coarse_lat(lat, bdims)
+    out = np.zeros(clat + (n, n), dtype=complex)
+    Wc = np.conj(W)
+    for sp in range(2):
+        for j in range(nv):
+            rows = blocks.block_sum_keep(Wc * op.pweight(W[sp, j]), lat, bdims, 2)
+            out[..., :, sp * nv + j] = np.moveaxis(rows.reshape((n,) + clat), 0, -1)
+    return out
+
+
 def build_coarse_operator(op, W, bdims):
-    """CoarseOperator for the next level: D_c(mu) = P^dagger D_W P + i mu Gamma5_c."""
-    return CoarseOperator(galerkin(op, W, bdims), W.shape[1])
+    """CoarseOperator for the next level: D_c(mu) = P^dagger D_W P + i mu Gamma5_c, with the
+    projected parity weight for different twists on even and odd sites."""
+    return CoarseOperator(galerkin(op, W, bdims), W.shape[1], Q=projected_pweight(op, W, bdims))

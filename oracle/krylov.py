@@ -26,6 +26,7 @@ x_o = 0, stopped on the recursively updated residual of the squared system.
 import numpy as np
 
 from .dirac import parity
+from .operators import negate_twist
 
 
 def _dot(a, b):
@@ -157,7 +158,7 @@ def eo_cg(op, b, mu, tol=1e-10, max_iter=100000):
         return odd * op.site(v_o * odd, m) - odd * op.hop(t)
 
     def d_hat_dag(v_o):
-        return op.gamma5(d_hat(op.gamma5(v_o), -mu))
+        return op.gamma5(d_hat(op.gamma5(v_o), negate_twist(mu)))
 
     b_e, b_o = b * even, b * odd
     rhat = b_o - odd * op.hop(op.site_inv(b_e, mu) * even)

@@ -12,7 +12,8 @@ Readings where the paper is silent:
   preconditioner application on level l is  x = P D_{l+1}^-1 R v  followed by
   ``post_smooth`` SAP cycles on D_l x = v started from that x;
 * only the coarsest level uses the shifted twist delta*mu (Table 1:
-  mu_coarse = 5.2 mu); every other level uses mu;
+  mu_coarse = 5.2 mu); every other level uses mu; a twist that differs on even
+  and odd sites is shifted on both parities alike;
 * setup iteration k = 1 runs the SAP smoother (``post_smooth`` cycles) on each
   test vector as right-hand side, iterations k >= 2 run one preconditioner
   application per test vector; after every iteration each vector is normalised
@@ -27,6 +28,7 @@ from typing import List, Tuple
 import numpy as np
 
 from . import aggregation, coarse, krylov, sap
+from .operators import scale_twist
 
 
 @dataclass
@@ -65,7 +67,8 @@ class Hierarchy:
         return self.p.nlevels
 
     def mu_at(self, level, mu):
-        return self.p.delta * mu if level == self.L - 1 else mu
+        """The coarsest level uses delta times the twist (both parities of a pair)."""
+        return scale_twist(mu, self.p.delta) if level == self.L - 1 else mu
 
     def rebuild(self, level, v):
         """Normalise test vectors v of level ``level``, build P and D_{level+1}."""

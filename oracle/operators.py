@@ -10,11 +10,41 @@ structure of the fine one), into
 * nearest-neighbour hops ``hop_dir(psi, d, sign)`` whose sum is ``hop``.
 
 ``apply(psi, mu) = site(psi, mu) + hop(psi)``.
+
+The twist ``mu`` is a number, or a pair ``(mu_e, mu_o)`` for a different twist
+on even and odd sites (a library feature of the paper's appendix, used by the
+even-odd preconditioned HMC): i Gamma5 (mu_e P_e + mu_o P_o) with P_e, P_o the
+projectors on even and odd sites.  Written as i Gamma5 (mbar + d S) with
+mbar = (mu_e + mu_o)/2, d = (mu_e - mu_o)/2 and S the site-local parity weight
+(+1 on even, -1 on odd sites), it keeps its form on every coarse level: the
+Galerkin product of i d Gamma5 S is i d Q Gamma5_c with
+Q_A = sum_{x in A} P_A(x)^dagger S(x) P_A(x) (Gamma5 P = P Gamma5_c), a dense
+site-local block that commutes with Gamma5_c; ``pweight`` applies S (or Q).
 """
 
 import numpy as np
 
 from . import dirac
+
+
+def split_twist(mu):
+    """(mbar, d) of a twist: a number mu gives (mu, 0), a pair (mu_e, mu_o) gives
+    ((mu_e + mu_o)/2, (mu_e - mu_o)/2)."""
+    if np.ndim(mu) == 0:
+        return float(mu), 0.0
+    mu_e, mu_o = mu
+    return 0.5 * (mu_e + mu_o), 0.5 * (mu_e - mu_o)
+
+
+def scale_twist(mu, f):
+    """f times a twist (both parities of a pair)."""
+    if np.ndim(mu) == 0:
+        return f * mu
+    return (f * mu[0], f * mu[1])
+
+
+def negate_twist(mu):
+    return scale_twist(mu, -1.0)
 
 
 class FineOperator:
@@ -29,19 +59,33 @@ class FineOperator:
         self.bc_t = bc_t
         self._g, self._g5 = dirac.gamma_matrices()
         self._g5_12 = np.kron(np.diag(self._g5).real, np.ones(3))  # gamma5 x I_3 diagonal
+        self._sgn = np.where(dirac.parity(self.lat) == 0, 1.0, -1.0)  # parity weight S(x)
+
+    def pweight(self, psi):
+        """S psi: +psi on even sites, -psi on odd sites."""
+        return self._sgn.reshape(self.lat + (1, 1)) * psi
 
     def apply(self, psi, mu):
-        return dirac.apply_D(self.U, self.S, psi, mu, self.bc_t, self.theta)
+        mb, d = split_twist(mu)
+        out = dirac.apply_D(self.U, self.S, psi, mb, self.bc_t, self.theta)
+        if d != 0.0:
+            out = out + dirac.apply_twist(self.pweight(psi), d)
+        return out
 
     def site(self, psi, mu):
+        mb, d = split_twist(mu)
         out = dirac.apply_site(self.S, psi)
-        if mu != 0.0:
-            out = out + dirac.apply_twist(psi, mu)
+        if mb != 0.0:
+            out = out + dirac.apply_twist(psi, mb)
+        if d != 0.0:
+            out = out + dirac.apply_twist(self.pweight(psi), d)
         return out
 
     def site_matrix(self, mu):
-        """(S(x) + i mu gamma5 x I_3) as a 12x12 matrix per site."""
-        return self.S + 1j * mu * np.diag(self._g5_12)
+        """(S(x) + i (mbar + d S(x)) gamma5 x I_3) as a 12x12 matrix per site."""
+        mb, d = split_twist(mu)
+        tw = (mb + d * self._sgn)[..., None, None]
+        return self.S + 1j * tw * np.diag(self._g5_12)
 
     def site_inv(self, psi, mu):
         """Per-site inverse of the site-local part, applied as (S + i mu gamma5)^-1 psi.
@@ -85,24 +129,38 @@ class CoarseOperator:
     shape ``lat + (2 Nv, 2 Nv)``; coarse dof index s*Nv + i.
     """
 
-    def __init__(self, blocks, nv):
+    def __init__(self, blocks, nv, Q=None):
         self.blocks = blocks
         self.lat = blocks.shape[1:5]
         self.nv = nv
         self.dof = (2 * nv,)
         self.g5c = np.concatenate([np.ones(nv), -np.ones(nv)])  # Gamma5_c = tau3 x I_Nv
+        self.Q = Q  # projected parity weight, lat + (2Nv, 2Nv) (None: parity twists not available)
 
     def _mv(self, A, v):
         return np.matmul(A, v[..., None])[..., 0]
 
+    def pweight(self, v):
+        """Q v, the parity weight projected to this level."""
+        if self.Q is None:
+            raise ValueError("coarse operator built without the projected parity weight")
+        return self._mv(self.Q, v)
+
     def site(self, v, mu):
+        mb, d = split_twist(mu)
         out = self._mv(self.blocks[0], v)
-        if mu != 0.0:
-            out = out + 1j * mu * self.g5c * v
+        if mb != 0.0:
+            out = out + 1j * mb * self.g5c * v
+        if d != 0.0:
+            out = out + 1j * d * self.pweight(self.g5c * v)
         return out
 
     def site_matrix(self, mu):
-        return self.blocks[0] + 1j * mu * np.diag(self.g5c)
+        mb, d = split_twist(mu)
+        M = self.blocks[0] + 1j * mb * np.diag(self.g5c)
+        if d != 0.0:
+            M = M + 1j * d * np.matmul(self.Q, np.diag(self.g5c))
+        return M
 
     def site_inv(self, v, mu):
         if getattr(self, "_inv_mu", None) != mu:
