@@ -72,6 +72,6 @@ def projected_pweight(op, W, bdims):
 
 
 def build_coarse_operator(op, W, bdims):
-    """CoarseOperator for the next level: D_c(mu) = P^dagger D_W P + i mu Gamma5_c, with the
-    projected parity weight for different twists on even and odd sites."""
-    return CoarseOperator(galerkin(op, W, bdims), W.shape[1], Q=projected_pweight(op, W, bdims))
+    """CoarseOperator for the next level: D_c(mu) = P^dagger D_W P + i mu Gamma5_c; the projected
+    parity weight (different twists on even and odd sites) is computed when first used."""
+    return CoarseOperator(galerkin(op, W, bdims), W.shape[1], Q_fn=lambda: projected_pweight(op, W, bdims))

@@ -129,13 +129,20 @@ class CoarseOperator:
     shape ``lat + (2 Nv, 2 Nv)``; coarse dof index s*Nv + i.
     """
 
-    def __init__(self, blocks, nv, Q=None):
+    def __init__(self, blocks, nv, Q=None, Q_fn=None):
         self.blocks = blocks
         self.lat = blocks.shape[1:5]
         self.nv = nv
         self.dof = (2 * nv,)
         self.g5c = np.concatenate([np.ones(nv), -np.ones(nv)])  # Gamma5_c = tau3 x I_Nv
-        self.Q = Q  # projected parity weight, lat + (2Nv, 2Nv) (None: parity twists not available)
+        self._Q = Q         # projected parity weight, lat + (2Nv, 2Nv), or
+        self._Q_fn = Q_fn   # a function computing it when first needed (None, None: not available)
+
+    @property
+    def Q(self):
+        if self._Q is None and self._Q_fn is not None:
+            self._Q = self._Q_fn()
+        return self._Q
 
     def _mv(self, A, v):
         return np.matmul(A, v[..., None])[..., 0]
