@@ -170,9 +170,7 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
   double2* h2 = h + nh;
   double2* y = h2 + nh;
   double2* nr2 = y + nh;
-  ad.scale = nr2 + R;
-  double2* unused = ad.scale + R;
-  (void)unused;
+  ad.scale = nr2 + R;  // (one more block of R stays reserved after it)
   ad.bn = (double*)(st2 + tot2);
   ad.est = ad.bn + R;
   ad.m = m;
