@@ -431,6 +431,37 @@ def test_preconditioner_error_propagation(fine, fine_dense, agg):
     assert np.linalg.norm(x - want) < 1e-9 * np.linalg.norm(want)
 
 
+def test_three_level_preconditioner_with_exact_level1_solve(fine, fine_dense, agg):
+    """Three levels with the level-1 FGMRES driven to 1e-14: the level-0 preconditioner equals the
+    two-level error propagation with the exact level-1 inverse, E_SAP^k (I - P D_1(mu)^-1 P^dagger D),
+    where level 1 (not the coarsest) keeps the twist mu.  Level-1 blocks of single sites on a 2^4
+    level-1 lattice keep the dense check small."""
+    Dm, mu = fine_dense
+    v, W = agg
+    nv = v.shape[0]
+    B1 = (1, 1, 1, 1)
+    p = mg.Params(nlevels=3, nv=[nv, 2], bdims=[B2, B1], post_smooth=2, nmr=120, kcycle_restart=64,
+                  kcycle_max_restarts=5, kcycle_tol=1e-14, coarse_restart=60, coarse_max_restarts=2,
+                  coarse_tol=1e-6, delta=5.2)
+    lat1 = blocks.coarse_lat(fine.lat, B2)
+    v1 = synth.gaussian_vectors((2,) + lat1 + (2 * nv,), seed=33).numpy()
+    h = mg.hierarchy_from_vectors(fine, p, [v, v1])
+    b = synth.gaussian_spinor(DIMS4, seed=12).numpy()
+    x = h.precondition(0, b, mu).ravel()
+    P = dense_P(fine, W, B2)
+    D0 = dense(lambda y: fine.apply(y, 0.0), fine.lat + fine.dof)
+    g5c = np.tile(np.concatenate([np.ones(nv), -np.ones(nv)]), P.shape[1] // (2 * nv))
+    D1 = P.conj().T @ D0 @ P + 1j * mu * np.diag(g5c)
+    sets = block_index_sets(fine, B2)
+    Br, Bb = block_inverse_dense(Dm, sets, 0), block_inverse_dense(Dm, sets, 1)
+    E = (np.eye(len(x)) - Bb @ Dm) @ (np.eye(len(x)) - Br @ Dm)
+    bv = b.ravel()
+    xs = np.linalg.solve(Dm, bv)
+    xc = P @ np.linalg.solve(D1, P.conj().T @ bv)
+    want = xs - E @ (E @ (xs - xc))
+    assert np.linalg.norm(x - want) < 1e-9 * np.linalg.norm(want)
+
+
 def test_two_level_solve_config_4x4x4x4(fine, fine_dense):
     """4^4, eps=0.3, kappa=0.125, c_sw=1.0, mu=0.01: the two-level solve reaches 1e-10 and
     agrees with the dense LU solution; the same setup also solves the -mu flavour."""
