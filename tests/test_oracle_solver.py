@@ -321,6 +321,22 @@ def test_galerkin_equals_dense_product(fine, fine_dense, agg):
                 assert np.max(np.abs(Dc[a * n:(a + 1) * n, b * n:(b + 1) * n])) == 0
 
 
+def test_galerkin_with_twisted_boundaries_is_dense_product():
+    """Twisted boundaries reach the coarse level through the per-direction hops: D_c = P^dagger D P
+    densely, with D the twisted operator (and antiperiodic t on top)."""
+    U = synth.gauge_field(DIMS4, 0.3, seed=5).numpy()
+    op = FineOperator(U, 0.125, 1.0, 1, theta=[0.6, -0.9, 1.4, 0.3])
+    nv = 3
+    v = synth.gaussian_vectors((nv,) + op.lat + op.dof, seed=8).numpy()
+    W = aggregation.build_P(op, v, B2)
+    cop = coarse.build_coarse_operator(op, W, B2)
+    mu = 0.04
+    P = dense_P(op, W, B2)
+    want = P.conj().T @ dense(lambda y: op.apply(y, mu), op.lat + op.dof) @ P
+    got = dense(lambda y: cop.apply(y, mu), cop.lat + cop.dof)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
 @pytest.mark.parametrize("bc_t", [0, 1])
 def test_free_field_coarse_closed_form(bc_t):
     dims = (8, 4, 4, 8)           # T, X, Y, Z
