@@ -95,3 +95,25 @@ def test_dense_matrix_from_the_formula(dims, bc_t):
     want = brute_force_D(U, kappa, csw, mu, dims, bc_t)
     got = oracle_matrix(op, mu)
     assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("bc_t,theta", [(0, None), (1, None), (1, [0.5, -1.2, 0.8, 2.0])])
+def test_site_local_evaluation_matches_the_operator(bc_t, theta):
+    """oracle/local.py (D psi at chosen sites, for parity on lattices too large for a full oracle
+    application) equals the oracle's operator at every site of a 4 x 2 x 4 x 2 lattice and at random
+    sites of a 4^4 lattice, for periodic, antiperiodic and twisted boundaries."""
+    from oracle import local
+    for dims, allsites in (((4, 2, 4, 2), True), ((4, 4, 4, 4), False)):
+        U = synth.gauge_field(dims, 0.3, seed=2).numpy()
+        psi = synth.gaussian_spinor(dims, seed=3).numpy()
+        kappa, csw, mu = 0.13, 1.4, 0.07
+        full = dirac.apply_D(U, dirac.site_term(U, kappa, csw), psi, mu, bc_t, theta)
+        T, X, Y, Z = dims
+        if allsites:
+            sites = [(t, x, y, z) for t in range(T) for x in range(X) for y in range(Y) for z in range(Z)]
+        else:
+            rng = np.random.default_rng(4)
+            sites = [tuple(int(rng.integers(0, n)) for n in dims) for _ in range(24)]
+        got = local.apply_D_at_sites(U, kappa, csw, psi, mu, sites, bc_t, theta)
+        want = np.array([full[t, z, y, x] for (t, x, y, z) in sites])
+        assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
