@@ -59,3 +59,25 @@ def test_default_params_are_table_1(lib):
     assert (p.kcycle_restart, p.kcycle_max_restarts, p.kcycle_tol) == (5, 2, 0.1)
     assert (p.coarse_restart, p.coarse_max_restarts, p.coarse_tol, p.delta) == (100, 5, 0.1, 5.2)
     assert list(p.block[0]) == [4, 4, 4, 4] and list(p.block[1]) == [2, 2, 2, 2]
+
+
+def test_binding_rejects_bad_buffers_on_the_host(lib):
+    """The Python binding passes only C-contiguous complex128 buffers, refuses read-only outputs and
+    mixed host / device arguments, before any library call."""
+    import numpy as np
+
+    from paper_1610_02370_gb300 import ddtm
+    good = np.zeros((2, 3), dtype=np.complex128)
+    p, loc = ddtm._buf(good)
+    assert p == good.ctypes.data and loc == ddtm.LOC_HOST
+    for bad in (np.zeros((2, 3)), np.zeros((3, 2), dtype=np.complex128).T, [1.0 + 0j]):
+        with pytest.raises(TypeError):
+            ddtm._buf(bad)
+    ro = np.zeros(4, dtype=np.complex128)
+    ro.flags.writeable = False
+    ddtm._buf(ro)  # fine as an input
+    with pytest.raises(TypeError):
+        ddtm._buf(ro, writable=True)
+    with pytest.raises(TypeError):
+        ddtm._same_loc((1, ddtm.LOC_HOST), (2, ddtm.LOC_DEVICE))
+    assert ddtm._same_loc((1, ddtm.LOC_DEVICE), (2, ddtm.LOC_DEVICE)) == ddtm.LOC_DEVICE
