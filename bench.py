@@ -249,6 +249,23 @@ def oracle_unit_times(wl, sample_dims=(16, 8, 8, 8)):
     return out
 
 
+def host_cpu():
+    """Core count and CPU model of this host, recorded beside the CPU baseline (never raises)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            fields = {}
+            for line in f:
+                k, sep, v = line.partition(":")
+                if sep and v.strip():
+                    fields.setdefault(k.strip(), v.strip())
+        model = fields.get("model name") or (("CPU part " + fields["CPU part"]) if "CPU part" in fields else None)
+    except (OSError, ValueError):
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine() or "unknown"}
+
+
 ONE_THREAD = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
                                 "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
 
@@ -324,7 +341,7 @@ def reference_arm(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload + " propagator (12 point sources)", **{k: wl[k] for k in wl},
                        "mg": MG},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": "oracle building blocks timed on a %s lattice, scaled per site to %s and "
                                        "multiplied by the work units (right-hand sides, vectors) of one GPU step" % (
                                            unit["_sample"], args.workload)},
@@ -566,7 +583,7 @@ def main():
         per_step_counts = {k: {"launches": v["launches"] / args.steps, "units": v.get("units", v["launches"]) / args.steps}
                            for k, v in counts.items()}
         est, _ = oracle_estimate(unit, per_step_counts, V, Nc)
-        cpu = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": "oracle building blocks (D, SAP half-sweep, P, Galerkin, R, P, coarse even-odd GMRES "
                          "iteration) timed on a %s lattice with the same couplings and multigrid parameters, scaled "
                          "per site to %s and multiplied by this step's work units (right-hand sides and vectors "

@@ -73,3 +73,33 @@ def test_reference_arm_line_rank0():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_host_cpu_record_x86_and_arm(monkeypatch):
+    """The CPU baseline's host record reads the model name on x86 hosts and the CPU part on Arm hosts
+    (whose /proc/cpuinfo has no model name), and never fails."""
+    import builtins
+    import io
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    real_open = builtins.open
+    samples = {"x86": "processor\t: 0\nmodel name\t: Some CPU @ 2.0GHz\n",
+               "arm": "processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n"}
+    for kind, text in samples.items():
+        def fake_open(path, *a, text=text, **k):
+            if path == "/proc/cpuinfo":
+                return io.StringIO(text)
+            return real_open(path, *a, **k)
+        monkeypatch.setattr(builtins, "open", fake_open)
+        rec = bench.host_cpu()
+        assert rec["nproc"] == os.cpu_count()
+        assert rec["cpu_model"] == ("Some CPU @ 2.0GHz" if kind == "x86" else "CPU part 0xd4f")
+
+    def no_file(path, *a, **k):
+        if path == "/proc/cpuinfo":
+            raise OSError("no such file")
+        return real_open(path, *a, **k)
+    monkeypatch.setattr(builtins, "open", no_file)
+    assert bench.host_cpu()["cpu_model"]
