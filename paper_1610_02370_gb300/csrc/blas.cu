@@ -447,11 +447,7 @@ static const int DOTS_JB = 8;
 template <typename TV>
 static void maxpy_pairs_t(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev, double sign,
                           double2* npart, int G, int bd, cudaStream_t st) {
-  static bool cfg = false;
-  if (!cfg) {
-    CK(cudaFuncSetAttribute(k_bmaxpy_pairs<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    cfg = true;
-  }
+  set_dynamic_smem((const void*)k_bmaxpy_pairs<TV>, 200 * 1024);
   const size_t smem = (size_t)nvec * w.R * sizeof(float2);
   k_bmaxpy_pairs<TV><<<G, bd, smem, st>>>((float2*)w.p, (const TV*)V.p, ldv, nvec, coef_dev, w.n * w.R / 2, w.R,
                                           (float)sign, npart);
@@ -482,12 +478,8 @@ static int pairs_grid(const VSet& w, int bd, int nvec) {
 template <typename TV>
 static void dots_pairs_t(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* partial, int G, int bd,
                          cudaStream_t st) {
-  static bool cfg = false;
   const size_t smem = (size_t)bd * (4 * DOTS_JB + 1) * sizeof(float);
-  if (!cfg) {
-    CK(cudaFuncSetAttribute(k_bdots_pairs<DOTS_JB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-    cfg = true;
-  }
+  set_dynamic_smem((const void*)k_bdots_pairs<DOTS_JB, TV>, 64 * 1024);
   dim3 grid(G, (nvec + DOTS_JB - 1) / DOTS_JB);
   k_bdots_pairs<DOTS_JB, TV><<<grid, bd, smem, st>>>((const TV*)V.p, ldv, nvec, (const float4*)w.p,
                                                      w.n * w.R / 2, w.R, partial);
@@ -535,11 +527,7 @@ void Blas::norms2(const VSet& a, double* out_host) {
 template <typename A, typename B, bool INTER>
 static void maxpy_launch(dim3 grid, int bd, size_t smem, cudaStream_t st, B* w, const A* V, size_t ldv, int nvec,
                          const double2* dc, size_t n, int R, double sign, double2* npart) {
-  static bool cfg = false;
-  if (!cfg) {
-    CK(cudaFuncSetAttribute(k_bmaxpy<A, B, INTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    cfg = true;
-  }
+  set_dynamic_smem((const void*)k_bmaxpy<A, B, INTER>, 200 * 1024);
   k_bmaxpy<A, B, INTER><<<grid, bd, smem, st>>>(w, V, ldv, nvec, dc, n, R, sign, npart);
 }
 
@@ -790,19 +778,11 @@ void launch_arnoldi_step(const ArnoldiDev& a, int j, const double2* h, const dou
   const unsigned grid = (unsigned)((a.R + ARB - 1) / ARB);
   if (fp32) {
     size_t smem = (size_t)ARB * (3 * j + 2) * sizeof(cplx<float>);
-    static bool cfg = false;
-    if (!cfg) {
-      CK(cudaFuncSetAttribute(k_arnoldi_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      cfg = true;
-    }
+    set_dynamic_smem((const void*)k_arnoldi_step<float>, 200 * 1024);
     k_arnoldi_step<float><<<grid, 128, smem, st>>>(a, j, h, h2, hn2);
   } else {
     size_t smem = (size_t)ARB * (3 * j + 2) * sizeof(cplx<double>);
-    static bool cfg = false;
-    if (!cfg) {
-      CK(cudaFuncSetAttribute(k_arnoldi_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      cfg = true;
-    }
+    set_dynamic_smem((const void*)k_arnoldi_step<double>, 200 * 1024);
     k_arnoldi_step<double><<<grid, 128, smem, st>>>(a, j, h, h2, hn2);
   }
   CKL("arnoldi_step");

@@ -258,10 +258,10 @@ void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* D
   if (dprec != PREC_F32) throw Error(DDTM_ERR_ARG, "internal: Galerkin output is FP32");
   const size_t srows = galerkin_rows_smem(g, faces, nv);
   if (rows_fp16 && srows <= 220 * 1024) {
-    CK(cudaFuncSetAttribute(k_galerkin_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)srows));
+    set_dynamic_smem((const void*)k_galerkin_rows, srows);
     k_galerkin_rows<<<g.Nb * 2, threads, srows, st>>>((float2*)Dc, P, U, C, q, f, nv);
   } else {
-    CK(cudaFuncSetAttribute(k_galerkin<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_dynamic_smem((const void*)k_galerkin<float2>, smem);
     k_galerkin<float2><<<g.Nb, threads, smem, st>>>((float2*)Dc, P, U, C, q, f, nv);
   }
   CKL("galerkin");
@@ -566,11 +566,7 @@ static void coarse_even_t(const CoarseLevel& c, cplx<float>* t, const cplx<float
   unsigned grid = (unsigned)((ne + spb - 1) / spb);
   if (grid == 0) return;
   size_t smem = (size_t)spb * c.n * R * sizeof(cplx<float>);
-  static bool cfg = false;
-  if (!cfg) {
-    CK(cudaFuncSetAttribute(k_coarse_even<DS, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    cfg = true;
-  }
+  set_dynamic_smem((const void*)k_coarse_even<DS, RC>, 200 * 1024);
   k_coarse_even<DS, RC><<<grid, spb * per, smem, st>>>(t, rhs, v, c.Dc.as<DS>(), c.Dinv.as<float2>(), c.nbr_eo.as<int>(),
                                                        c.even.as<int>(), ne, c.n, R, sr, sh);
   CKL("coarse_even");
@@ -606,7 +602,7 @@ void launch_self_inverse(CoarseLevel& c, double mu_c, cudaStream_t st) {
   c.Dinv.ensure((size_t)ne * c.n * c.n * sizeof(float2));
   size_t smem = (size_t)c.n * 2 * c.n * sizeof(cplx<double>);
   int threads = ((c.n + 31) / 32) * 32;
-  CK(cudaFuncSetAttribute(k_self_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  set_dynamic_smem((const void*)k_self_inverse<float2>, smem);
   k_self_inverse<float2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(), c.n, c.nv, mu_c);
   CKL("self_inverse");
   if (c.prec == PREC_F16) build_inverse_images(c, st);

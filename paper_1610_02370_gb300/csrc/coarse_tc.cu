@@ -462,11 +462,7 @@ void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t
     const int grid = p.nout < cps * num_sms() ? p.nout : cps * num_sms();
 #define TC_LAUNCH(K)                                                                                    \
   case K: {                                                                                           \
-    static bool cfg = false;                                                                          \
-    if (!cfg) {                                                                                       \
-      CK(cudaFuncSetAttribute(k_coarse_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_1 + 1024)); \
-      cfg = true;                                                                                     \
-    }                                                                                                 \
+    set_dynamic_smem((const void*)k_coarse_tc<K>, TC_SMEM_1 + 1024);                                  \
     k_coarse_tc<K><<<grid, 192, smem, st>>>(a);                                                       \
     break;                                                                                            \
   }

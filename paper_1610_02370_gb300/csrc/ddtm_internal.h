@@ -26,6 +26,11 @@ void cuda_check(cudaError_t e, const char* what);
 void cuda_check_launch(const char* what);
 long kernel_launches();
 #define CK(x) ::ddtm::cuda_check((x), #x)
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute belongs to a (kernel, device) pair, so the
+// limits already set are remembered per pair; safe to call from several host
+// threads.
+void set_dynamic_smem(const void* kernel, size_t bytes);
 #define CKL(what) ::ddtm::cuda_check_launch(what)
 
 // Owned device allocation.

@@ -8,6 +8,9 @@
 // the global parity (t + x + y + z) mod 2, and each x-row of a block holds
 // alternating parities, which makes (parity, lexloc >> 1) a bijection.
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 #include "ddtm_internal.h"
@@ -27,6 +30,18 @@ void cuda_check(cudaError_t e, const char* what) {
     int code = (e == cudaErrorMemoryAllocation) ? DDTM_ERR_OOM : DDTM_ERR_CUDA;
     throw Error(code, std::string(what) + ": " + cudaGetErrorString(e));
   }
+}
+
+void set_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex m;
+  static std::map<std::pair<const void*, int>, size_t> set;  // (kernel, device) -> limit set
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(m);
+  size_t& have = set[std::make_pair(kernel, dev)];
+  if (bytes <= have) return;
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
 }
 
 void DevBuf::release() {

@@ -209,11 +209,7 @@ static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void*
   typedef typename Prec<P>::real R;
   Geo q{g.Vb, g.Nb, g.loc_nbr.as<uint32_t>(), g.blk_nbr.as<int>()};
   size_t smem = sap_smem_bytes(g.Vb, P);
-  static size_t configured = 0;
-  if (smem > configured) {
-    CK(cudaFuncSetAttribute(k_sap_half<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  set_dynamic_smem((const void*)k_sap_half<P>, smem);
   SapArgs<R> a{blocks, zero_blocks, zero_x, nmr, (R)mu, (size_t)g.V * 12, g.V};
   dim3 grid(nrhs, nblocks);
   k_sap_half<P><<<grid, sap_threads(g.Vb), smem, s>>>(

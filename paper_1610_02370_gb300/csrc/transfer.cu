@@ -229,11 +229,7 @@ template <int PI, typename PS>
 static void restrict_p(const FineGeom& g, cplx<float>* c, Spinor<PI> f, size_t fstride, const PS* P, int nv, int R,
                        int Rs, cudaStream_t st) {
   size_t smem = (size_t)RST_RC * 12 * g.Vb * sizeof(cplx<float>);
-  static bool cfg = false;
-  if (!cfg) {
-    CK(cudaFuncSetAttribute(k_restrict<PI, PS, RST_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    cfg = true;
-  }
+  set_dynamic_smem((const void*)k_restrict<PI, PS, RST_RC>, 200 * 1024);
   dim3 grid(g.Nb, (R + RST_RC - 1) / RST_RC);
   k_restrict<PI, PS, RST_RC><<<grid, 256, smem, st>>>(c, f, fstride, g.V, P, nv, R, Rs);
 }
