@@ -1,0 +1,99 @@
+"""Parity at the benchmark's full size (32^3 x 64, the propagator workload of bench.py): D(mu) in FP64, FP32
+and FP16 storage at sampled sites against the site-local oracle (oracle/local.py), and properties that hold
+at any size on the library's own operators there: Gamma5-hermiticity of D(mu) in FP64 and of the
+tensor-core coarse operator built by the benchmark's setup."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import local
+from paper_1610_02370_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (64, 32, 32, 32)  # T, X, Y, Z
+EPS, KAPPA, CSW, MU = 0.12, 0.1372, 1.5755, 0.0015
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1610_02370_gb300 import build
+    build.build()
+    from paper_1610_02370_gb300 import ddtm
+    return ddtm
+
+
+@pytest.fixture(scope="module")
+def full(lib):
+    U = synth.gauge_field(DIMS, EPS, seed=0)
+    ctx = lib.ddtm_create(DIMS, (4, 4, 4, 4), 0)
+    lib.ddtm_load_gauge(ctx, U.cuda(), KAPPA, CSW)
+    yield lib, ctx, U
+    lib.ddtm_destroy(ctx)
+
+
+def sampled_sites():
+    rng = np.random.default_rng(17)
+    T, X, Y, Z = DIMS
+    sites = [tuple(int(rng.integers(0, n)) for n in DIMS) for _ in range(56)]
+    # the corners of the lattice: every hop of these wraps
+    sites += [(t, x, y, z) for t in (0, T - 1) for x in (0, X - 1) for y in (0,) for z in (0, Z - 1)]
+    return sites
+
+
+def test_dirac_full_size_sampled_sites(full):
+    lib, ctx, U = full
+    x = synth.gaussian_spinor(DIMS, seed=1)
+    sites = sampled_sites()
+    want = local.apply_D_at_sites(U.numpy(), KAPPA, CSW, x.numpy(), MU, sites)
+    idx = tuple(torch.tensor([s[k] for s in sites]) for k in (0, 3, 2, 1))  # (t, z, y, x) array order
+    for prec, tol in ((lib.PREC_F64, 1e-13), (lib.PREC_F32, 2e-6), (lib.PREC_F16, 2e-3)):
+        y = torch.zeros_like(x).cuda()
+        lib.ddtm_apply_D(ctx, y, x.cuda(), 1, MU, prec)
+        got = y.cpu()[idx].numpy()
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
+
+
+def g5(v):
+    w = v.clone()
+    w[..., 2:, :] *= -1
+    return w
+
+
+def test_dirac_full_size_gamma5_hermiticity(full):
+    lib, ctx, _ = full
+    v = synth.gaussian_spinor(DIMS, seed=2).cuda()
+    w = synth.gaussian_spinor(DIMS, seed=3).cuda()
+    a = torch.zeros_like(v)
+    lib.ddtm_apply_D(ctx, a, g5(v), 1, MU, lib.PREC_F64)
+    lhs = torch.vdot(w.flatten(), g5(a).flatten())
+    bb = torch.zeros_like(w)
+    lib.ddtm_apply_D(ctx, bb, w, 1, -MU, lib.PREC_F64)
+    rhs = torch.vdot(bb.flatten(), v.flatten())
+    assert abs((lhs - rhs).item()) <= 1e-12 * abs(lhs.item())
+
+
+def test_coarse_operator_full_size_gamma5_hermiticity(full):
+    """After the benchmark's setup (Nv = 24, 4^4 aggregates, FP16 tensor-core coarse operator):
+    <u, D_c(mu) v> = <Gamma5_c D_c(-mu) Gamma5_c u, v> within the FP16 storage accuracy."""
+    lib, ctx, _ = full
+    p = lib.ddtm_get_params(ctx)
+    p.nv[0] = 24
+    p.n_setup = 6
+    p.post_smooth = 2
+    p.coarse_prec = lib.PREC_F16
+    lib.ddtm_set_params(ctx, p)
+    lib.ddtm_setup(ctx, MU, 2024)
+    cl = tuple(d // 4 for d in (DIMS[0], DIMS[3], DIMS[2], DIMS[1]))
+    u = synth.gaussian_vectors(cl + (48,), seed=4).cuda()
+    v = synth.gaussian_vectors(cl + (48,), seed=5).cuda()
+    g5c = torch.cat([torch.ones(24), -torch.ones(24)]).to(torch.complex128).cuda()
+    a = torch.zeros_like(v)
+    lib.ddtm_apply_Dc(ctx, 1, a, v, 1, MU)
+    lhs = torch.vdot(u.flatten(), a.flatten())
+    bq = torch.zeros_like(u)
+    lib.ddtm_apply_Dc(ctx, 1, bq, (g5c * u).contiguous(), 1, -MU)
+    rhs = torch.vdot((g5c * bq).flatten(), v.flatten())
+    scale = torch.linalg.norm(u) * torch.linalg.norm(a)
+    assert abs((lhs - rhs).item()) <= 2e-3 * scale.item()
