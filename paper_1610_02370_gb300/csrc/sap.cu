@@ -210,12 +210,17 @@ static void launch_sap_half_t(const FineGeom& g, void* x, float* xn, const void*
   Geo q{g.Vb, g.Nb, g.loc_nbr.as<uint32_t>(), g.blk_nbr.as<int>()};
   size_t smem = sap_smem_bytes(g.Vb, P);
   set_dynamic_smem((const void*)k_sap_half<P>, smem);
-  SapArgs<R> a{blocks, zero_blocks, zero_x, nmr, (R)mu, (size_t)g.V * 12, g.V};
-  dim3 grid(nrhs, nblocks);
-  k_sap_half<P><<<grid, sap_threads(g.Vb), smem, s>>>(
-      Spinor<P>{(S*)x, xn, g.Vb}, Spinor<P>{(S*)b, (float*)bn, g.Vb}, Links<P>{(const S*)links, g.Vb},
-      Clover<P>{(const S*)clover, g.Vb}, SiteInv<P>{(const S*)sinv, g.Vb / 2}, q, a);
-  CKL("sap_half");
+  // grid.y is at most 65535: on large lattices (e.g. 128 x 64^3 with 4^4 blocks, 65536 blocks per
+  // colour) the blocks of the colour go in several launches, which is exact since they are independent
+  for (int b0 = 0; b0 < nblocks; b0 += 65535) {
+    const int nb = nblocks - b0 < 65535 ? nblocks - b0 : 65535;
+    SapArgs<R> a{blocks + b0, zero_blocks + b0, zero_x, nmr, (R)mu, (size_t)g.V * 12, g.V};
+    dim3 grid(nrhs, nb);
+    k_sap_half<P><<<grid, sap_threads(g.Vb), smem, s>>>(
+        Spinor<P>{(S*)x, xn, g.Vb}, Spinor<P>{(S*)b, (float*)bn, g.Vb}, Links<P>{(const S*)links, g.Vb},
+        Clover<P>{(const S*)clover, g.Vb}, SiteInv<P>{(const S*)sinv, g.Vb / 2}, q, a);
+    CKL("sap_half");
+  }
 }
 
 void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,
