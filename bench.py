@@ -138,6 +138,7 @@ def parse_args():
     ap.add_argument("--workload", default="32x32x32x64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--oracle-units", default=None, help=argparse.SUPPRESS)  # child process of the CPU baseline
     return ap.parse_args()
@@ -279,6 +280,45 @@ def oracle_unit_times_one_core(workload):
     if r.returncode != 0:
         raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def host_cores():
+    """Host cores this process may run on (its affinity mask, else the CPU count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_unit_times_all_cores(workload, ncores=None):
+    """oracle_unit_times in one single-threaded child process per host core, all running at once: each
+    child times the building blocks under full-node load, so the node does ncores units of work in the
+    time one child takes for one.  Returns the children's mean unit times divided by ncores (seconds per
+    unit of work with every core busy) and ncores."""
+    ncores = ncores or host_cores()
+    env = dict(os.environ, **ONE_THREAD)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-units", workload]
+    procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for _ in range(ncores)]
+    outs, err = [], None
+    for p in procs:
+        try:
+            o, e = p.communicate(timeout=1800)
+        except subprocess.TimeoutExpired:
+            p.kill()  # this child only
+            o, e = p.communicate()
+            err = err or "an oracle child timed out"
+            continue
+        if p.returncode != 0:
+            err = err or ("oracle timing failed: " + e[-500:])
+            continue
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    if err:
+        raise RuntimeError(err)
+    keys = [k for k in outs[0] if not k.startswith("_")]
+    unit = {k: statistics.mean(o[k] for o in outs) / ncores for k in keys}
+    unit["_sample"] = outs[0]["_sample"]
+    return unit, ncores
 
 
 def oracle_estimate(unit, counts, V, Nc):
@@ -590,6 +630,16 @@ def main():
                          "processed per kernel family)" % (
                              unit["_sample"], args.workload),
                "unit_s_per_site": {k: v for k, v in unit.items() if not k.startswith("_")}}
+        if not args.no_cpu_all:
+            # the same oracle on every host core at once (one single-threaded process per core)
+            try:
+                unit_all, ncores = oracle_unit_times_all_cores(args.workload)
+                est_all, _ = oracle_estimate(unit_all, per_step_counts, V, Nc)
+                cpu["all_cores"] = {"value": est_all, "unit": UNIT, "cores": ncores,
+                                    "method": "one single-threaded oracle process per host core, all timing the "
+                                              "same sample at once; seconds per unit = their mean / cores"}
+            except (RuntimeError, OSError, ValueError) as e:
+                cpu["all_cores"] = {"value": None, "error": str(e)[:300]}
 
     if rank == 0:
         line = {
