@@ -638,7 +638,7 @@ def main():
                 cpu["all_cores"] = {"value": est_all, "unit": UNIT, "cores": ncores,
                                     "method": "one single-threaded oracle process per host core, all timing the "
                                               "same sample at once; seconds per unit = their mean / cores"}
-            except (RuntimeError, OSError, ValueError) as e:
+            except (RuntimeError, OSError, ValueError, IndexError, KeyError) as e:
                 cpu["all_cores"] = {"value": None, "error": str(e)[:300]}
 
     if rank == 0:
