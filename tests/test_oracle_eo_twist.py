@@ -14,7 +14,7 @@ Gamma5_hat is inverted; Sec. 3.1 and the HMC figure).
 import numpy as np
 import pytest
 
-from oracle import aggregation, blocks, coarse, dirac, mg
+from oracle import aggregation, blocks, coarse, dirac, mg, sap
 from oracle.operators import FineOperator
 from paper_1610_02370_gb300 import synth
 
@@ -134,3 +134,64 @@ def test_two_level_solve_with_pair(fine):
     Dm = dense(lambda y: fine.apply(y, PAIR), fine.lat + fine.dof)
     xs = np.linalg.solve(Dm, b.ravel())
     assert np.linalg.norm(x.ravel() - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def block_sets(lat, bdims, nd):
+    """(dofs, colour) of every block, sites in canonical order."""
+    cl = blocks.coarse_lat(lat, bdims)
+    ab = blocks.axis_blocks(lat, bdims)
+    idx = np.indices(lat)
+    cidx = [idx[a] // ab[a] for a in range(4)]
+    bid = np.ravel_multi_index(cidx, cl).ravel()
+    colour = (sum(cidx) % 2).ravel()
+    out = []
+    for b in range(int(np.prod(cl))):
+        sites = np.flatnonzero(bid == b)
+        out.append(((sites[:, None] * nd + np.arange(nd)[None, :]).ravel(), colour[sites[0]]))
+    return out
+
+
+def one_sap_cycle_dense(Dm, sets, bv):
+    """Red blocks then black, each block solved exactly on the recomputed residual."""
+    x = np.zeros_like(bv)
+    for colour in (0, 1):
+        r = bv - Dm @ x
+        for dofs, c in sets:
+            if c == colour:
+                x[dofs] += np.linalg.solve(Dm[np.ix_(dofs, dofs)], r[dofs])
+    return x
+
+
+@pytest.mark.parametrize("eo", [True, False])
+def test_sap_with_pair_equals_dense_block_inverses(fine, eo):
+    """SAP (Sec. 2.4) with the twist pair and MR run to convergence equals one red-black cycle of exact
+    solves with the diagonal blocks of the dense D(mu_e, mu_o): the smoother sees the pair through its
+    site terms (even-odd: A_ee^-1 at mu_e, A_oo at mu_o) and nowhere else."""
+    Dm = dense(lambda x: fine.apply(x, PAIR), fine.lat + fine.dof)
+    b = synth.gaussian_spinor(DIMS4, seed=41).numpy()
+    want = one_sap_cycle_dense(Dm, block_sets(fine.lat, B2, 12), b.ravel())
+    got = sap.sap(fine, b, PAIR, B2, ncycles=1, nmr=150, eo=eo).ravel()
+    assert np.linalg.norm(got - want) < 1e-10 * np.linalg.norm(want)
+
+
+def test_coarse_sap_with_pair_equals_dense_block_inverses():
+    """The same on a coarse operator carrying a parity weight Q (the level-1 smoother of three levels
+    under a twist pair): random nearest-neighbour blocks and a random Hermitian Q that commutes with
+    Gamma5_c on a 4^4 coarse lattice, 2^4 blocks, even-odd and full block solves."""
+    from oracle.operators import CoarseOperator
+    rng = np.random.default_rng(44)
+    lat, nv = (4, 4, 4, 4), 2
+    n = 2 * nv
+    bl = 0.12 * (rng.standard_normal((9,) + lat + (n, n)) + 1j * rng.standard_normal((9,) + lat + (n, n)))
+    bl[0] += 1.5 * np.eye(n)
+    A = rng.standard_normal(lat + (n, n)) + 1j * rng.standard_normal(lat + (n, n))
+    Q = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
+    Q[..., :nv, nv:] = 0
+    Q[..., nv:, :nv] = 0
+    cop = CoarseOperator(bl, nv, Q=Q)
+    Dm = dense(lambda x: cop.apply(x, PAIR), cop.lat + cop.dof)
+    b = rng.standard_normal(lat + (n,)) + 1j * rng.standard_normal(lat + (n,))
+    want = one_sap_cycle_dense(Dm, block_sets(lat, B2, n), b.ravel())
+    for eo in (True, False):
+        got = sap.sap(cop, b, PAIR, B2, ncycles=1, nmr=150, eo=eo).ravel()
+        assert np.linalg.norm(got - want) < 1e-10 * np.linalg.norm(want), eo
