@@ -72,7 +72,7 @@ def test_reference_arm_line_rank0():
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
-    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
 
 
 def test_host_cpu_record_x86_and_arm(monkeypatch):
@@ -103,3 +103,22 @@ def test_host_cpu_record_x86_and_arm(monkeypatch):
         return real_open(path, *a, **k)
     monkeypatch.setattr(builtins, "open", no_file)
     assert bench.host_cpu()["cpu_model"]
+
+
+def test_oracle_estimate_bookkeeping():
+    """The CPU estimate multiplies each kernel family's work units of a GPU step by the oracle's time per
+    unit: with every unit time 1 it is the sum of the families' units (per site for the fine kernels, per
+    coarse site for the coarse iterations), and the coarse rhs-iterations are the tensor-core passes."""
+    import bench
+    counts = bench.REFERENCE_COUNTS
+    unit = {k: 1.0 for k in ("dslash", "sap_half", "build_P", "galerkin", "restrict", "prolong", "coarse_iter")}
+    V, Nc = 1000.0, 10.0
+    t, iters = bench.oracle_estimate(unit, counts, V, Nc)
+    assert iters == counts["coarse_tc_hop_even"]["units"]
+    fine_units = (counts["dslash_f32"]["units"] + counts["dslash_f64"]["units"] + counts["sap_half_f16"]["units"]
+                  + counts["build_P"]["launches"] + counts["galerkin"]["launches"]
+                  + counts["restrict_f16"]["units"] + counts["prolong_f16"]["units"])
+    assert t == fine_units * V + iters * Nc
+    # each family scales with its own unit time only
+    t2, _ = bench.oracle_estimate(dict(unit, galerkin=3.0), counts, V, Nc)
+    assert t2 - t == 2.0 * counts["galerkin"]["launches"] * V
