@@ -1,5 +1,5 @@
-"""Oracle: D(mu) psi evaluated at chosen sites only (Sec. 2.1), for parity checks on lattices too large
-for a full oracle application.
+"""Oracle: D(mu) psi evaluated at chosen sites only (Sec. 2.1), and one red-black SAP cycle (Sec. 2.4)
+evaluated at chosen blocks, for parity checks on lattices too large for a whole-lattice oracle run.
 
 TEST INFRASTRUCTURE ONLY.  The operator is local: (D psi)(x) needs psi and the links within one hop of
 x, and the clover term at x needs the links of the four plaquette leaves around x in every plane.  Each
@@ -85,3 +85,97 @@ def apply_D_at_sites(U, kappa, c_sw, psi, mu, sites, bc_t=0, theta=None):
             v = v - 0.5 * fb * (np.kron(i4 + g[d], _link(U, L, bwd, d).conj().T) @ spinor(bwd))
         out[n] = v
     return out.reshape(len(sites), 4, 3)
+
+
+# ---- one red-black SAP cycle (Sec. 2.4) at chosen blocks, for parity on lattices too large for the
+# whole-lattice oracle.  From x = 0, the red blocks' result depends only on b in the block; a black
+# block's residual needs the red solutions of its neighbouring blocks, whose hops reach it.
+
+def block_sites(bdims, bcoord):
+    """Sites (t, x, y, z) of the block at block coordinates bcoord, in lexical order."""
+    o = [bcoord[k] * bdims[k] for k in range(4)]
+    return [(o[0] + t, o[1] + x, o[2] + y, o[3] + z)
+            for t in range(bdims[0]) for x in range(bdims[1]) for y in range(bdims[2]) for z in range(bdims[3])]
+
+
+def block_matrix(U, kappa, c_sw, mu, sites):
+    """Dense matrix of the block operator D_BB + i mu Gamma5: the site terms and the hops between sites
+    of the block; hops that leave the block are dropped (Dirichlet block boundaries, Sec. 2.4).  A block
+    never wraps around the lattice, so no boundary phase enters."""
+    T, Z, Y, X = U.shape[:4]
+    L = (T, X, Y, Z)
+    g, g5 = gamma_matrices()
+    i4 = np.eye(4)
+    index = {s: i for i, s in enumerate(sites)}
+    n = 12 * len(sites)
+    A = np.zeros((n, n), dtype=complex)
+    tw = 1j * mu * np.kron(g5, np.eye(3))
+    for i, s in enumerate(sites):
+        A[12 * i:12 * i + 12, 12 * i:12 * i + 12] = site_term_at(U, kappa, c_sw, s) + tw
+        for d in range(4):
+            fwd, bwd = tuple(_step(s, d, 1)), tuple(_step(s, d, -1))
+            if fwd in index:
+                j = index[fwd]
+                A[12 * i:12 * i + 12, 12 * j:12 * j + 12] += -0.5 * np.kron(i4 - g[d], _link(U, L, s, d))
+            if bwd in index:
+                j = index[bwd]
+                A[12 * i:12 * i + 12, 12 * j:12 * j + 12] += -0.5 * np.kron(i4 + g[d], _link(U, L, bwd, d).conj().T)
+    return A
+
+
+def eo_block_mr(A, r, sites, nmr):
+    """The even-odd block solve of the SAP smoother (Sec. 2.4, 2.5) on the dense block matrix: nmr
+    minimal-residual steps from 0 on A_hat e_o = r_o - A_oe A_ee^-1 r_e with
+    A_hat = A_oo - A_oe A_ee^-1 A_eo, then e_e = A_ee^-1 (r_e - A_eo e_o).  A_ee is site-local."""
+    par = np.repeat([sum(s) % 2 for s in sites], 12)
+    E, O = np.flatnonzero(par == 0), np.flatnonzero(par == 1)
+    Aee_inv = np.zeros((len(E), len(E)), dtype=complex)
+    for k in range(0, len(E), 12):
+        Aee_inv[k:k + 12, k:k + 12] = np.linalg.inv(A[np.ix_(E[k:k + 12], E[k:k + 12])])
+    Aeo, Aoe, Aoo = A[np.ix_(E, O)], A[np.ix_(O, E)], A[np.ix_(O, O)]
+    Ahat = Aoo - Aoe @ Aee_inv @ Aeo
+    rho = r[O] - Aoe @ (Aee_inv @ r[E])
+    eo = np.zeros_like(rho)
+    for _ in range(nmr):
+        p = Ahat @ rho
+        den = np.vdot(p, p).real
+        al = np.vdot(p, rho) / den if den > 0 else 0.0
+        eo = eo + al * rho
+        rho = rho - al * p
+    e = np.zeros_like(r)
+    e[O] = eo
+    e[E] = Aee_inv @ (r[E] - Aeo @ eo)
+    return e
+
+
+def sap_cycle_at_block(U, kappa, c_sw, b, mu, bdims, bcoord, nmr, bc_t=0):
+    """x on the block at bcoord after one SAP cycle from x = 0 (red blocks, block colour
+    sum(bcoord) mod 2 = 0, then black), each block solved by eo_block_mr; returns (nsites, 4, 3)."""
+    T, Z, Y, X = U.shape[:4]
+    NB = (T // bdims[0], X // bdims[1], Y // bdims[2], Z // bdims[3])
+
+    def spinors(sites, field):
+        return np.concatenate([field[t, z, y, x].reshape(12) for (t, x, y, z) in sites])
+
+    def red_solve(bc):
+        sites = block_sites(bdims, bc)
+        return sites, eo_block_mr(block_matrix(U, kappa, c_sw, mu, sites), spinors(sites, b), sites, nmr)
+
+    sites = block_sites(bdims, bcoord)
+    if sum(bcoord) % 2 == 0:
+        return red_solve(bcoord)[1].reshape(len(sites), 4, 3)
+    # black: r_B = b_B - (D x_red)_B with x_red the red solutions on the neighbouring blocks
+    neighbours = set()
+    for d in range(4):
+        for s in (1, -1):
+            bc = list(bcoord)
+            bc[d] = (bc[d] + s) % NB[d]
+            neighbours.add(tuple(bc))
+    x = np.zeros_like(b)
+    for bc in neighbours:
+        rs, e = red_solve(bc)
+        for k, (t, xx, y, z) in enumerate(rs):
+            x[t, z, y, xx] = e[12 * k:12 * k + 12].reshape(4, 3)
+    r = spinors(sites, b) - apply_D_at_sites(U, kappa, c_sw, x, mu, sites, bc_t).reshape(-1)
+    e = eo_block_mr(block_matrix(U, kappa, c_sw, mu, sites), r, sites, nmr)
+    return e.reshape(len(sites), 4, 3)

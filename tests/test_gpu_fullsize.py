@@ -97,3 +97,23 @@ def test_coarse_operator_full_size_gamma5_hermiticity(full):
     rhs = torch.vdot((g5c * bq).flatten(), v.flatten())
     scale = torch.linalg.norm(u) * torch.linalg.norm(a)
     assert abs((lhs - rhs).item()) <= 2e-3 * scale.item()
+
+
+def test_sap_full_size_sampled_blocks(full):
+    """One SAP cycle (Sec. 2.4; 3 MR steps per even-odd reduced 4^4 block, red then black) from x = 0 at
+    the benchmark's full size, the smoother of the benchmark, against the block-local oracle at two red and
+    two black blocks, the lattice's corner blocks among them (their neighbours wrap around), in FP64 /
+    FP32 / FP16 storage within 1e-12 / 2e-6 / 2e-3."""
+    lib, ctx, U = full
+    B = (4, 4, 4, 4)
+    b = synth.gaussian_spinor(DIMS, seed=6)
+    bl = [(0, 0, 0, 0), (15, 7, 7, 7), (1, 0, 0, 0), (15, 7, 7, 6)]  # red, red, black, black
+    assert [sum(c) % 2 for c in bl] == [0, 0, 1, 1]
+    want = np.concatenate([local.sap_cycle_at_block(U.numpy(), KAPPA, CSW, b.numpy(), MU, B, c, 3) for c in bl])
+    sites = [s for c in bl for s in local.block_sites(B, c)]
+    idx = tuple(torch.tensor([s[k] for s in sites]) for k in (0, 3, 2, 1))  # (t, z, y, x) array order
+    for prec, tol in ((lib.PREC_F64, 1e-12), (lib.PREC_F32, 2e-6), (lib.PREC_F16, 2e-3)):
+        x = torch.zeros_like(b).cuda()
+        lib.ddtm_sap(ctx, x, b.cuda(), 1, MU, 1, 3, prec)
+        got = x.cpu()[idx].numpy()
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), prec

@@ -117,3 +117,20 @@ def test_site_local_evaluation_matches_the_operator(bc_t, theta):
         got = local.apply_D_at_sites(U, kappa, csw, psi, mu, sites, bc_t, theta)
         want = np.array([full[t, z, y, x] for (t, x, y, z) in sites])
         assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("bc_t", [0, 1])
+def test_sap_cycle_at_blocks_matches_the_whole_lattice_sap(bc_t):
+    """oracle/local.py's SAP cycle at chosen blocks (dense block matrices, for parity on lattices too
+    large for the whole-lattice oracle) equals the oracle's SAP (one cycle from x = 0, even-odd block MR,
+    3 steps) on an 8^4 lattice with 4^4 blocks, at a red and at a black block."""
+    from oracle import local, sap
+    dims, B = (8, 8, 8, 8), (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=3).numpy()
+    b = synth.gaussian_spinor(dims, seed=4).numpy()
+    kappa, csw, mu = 0.13, 1.4, 0.05
+    full = sap.sap(FineOperator(U, kappa, csw, bc_t), b, mu, B, ncycles=1, nmr=3, eo=True)
+    for bc in ((0, 0, 0, 0), (1, 1, 1, 0)):
+        got = local.sap_cycle_at_block(U, kappa, csw, b, mu, B, bc, 3, bc_t)
+        want = np.array([full[t, z, y, x] for (t, x, y, z) in local.block_sites(B, bc)])
+        assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
