@@ -74,10 +74,10 @@ def test_dirac_full_size_gamma5_hermiticity(full):
     assert abs((lhs - rhs).item()) <= 1e-12 * abs(lhs.item())
 
 
-def test_coarse_operator_full_size_gamma5_hermiticity(full):
-    """After the benchmark's setup (Nv = 24, 4^4 aggregates, FP16 tensor-core coarse operator):
-    <u, D_c(mu) v> = <Gamma5_c D_c(-mu) Gamma5_c u, v> within the FP16 storage accuracy."""
-    lib, ctx, _ = full
+@pytest.fixture(scope="module")
+def bench_setup(full):
+    """The benchmark's setup (Nv = 24, 4^4 aggregates, 6 iterations, FP16 tensor-core coarse operator)."""
+    lib, ctx, U = full
     p = lib.ddtm_get_params(ctx)
     p.nv[0] = 24
     p.n_setup = 6
@@ -85,9 +85,19 @@ def test_coarse_operator_full_size_gamma5_hermiticity(full):
     p.coarse_prec = lib.PREC_F16
     lib.ddtm_set_params(ctx, p)
     lib.ddtm_setup(ctx, MU, 2024)
-    cl = tuple(d // 4 for d in (DIMS[0], DIMS[3], DIMS[2], DIMS[1]))
-    u = synth.gaussian_vectors(cl + (48,), seed=4).cuda()
-    v = synth.gaussian_vectors(cl + (48,), seed=5).cuda()
+    return lib, ctx, U
+
+
+def coarse_shape():
+    return tuple(d // 4 for d in (DIMS[0], DIMS[3], DIMS[2], DIMS[1])) + (48,)  # (Tc, Zc, Yc, Xc, 2 Nv)
+
+
+def test_coarse_operator_full_size_gamma5_hermiticity(bench_setup):
+    """After the benchmark's setup: <u, D_c(mu) v> = <Gamma5_c D_c(-mu) Gamma5_c u, v> within the FP16
+    storage accuracy."""
+    lib, ctx, _ = bench_setup
+    u = synth.gaussian_vectors(coarse_shape(), seed=4).cuda()
+    v = synth.gaussian_vectors(coarse_shape(), seed=5).cuda()
     g5c = torch.cat([torch.ones(24), -torch.ones(24)]).to(torch.complex128).cuda()
     a = torch.zeros_like(v)
     lib.ddtm_apply_Dc(ctx, 1, a, v, 1, MU)
@@ -117,3 +127,22 @@ def test_sap_full_size_sampled_blocks(full):
         lib.ddtm_sap(ctx, x, b.cuda(), 1, MU, 1, 3, prec)
         got = x.cpu()[idx].numpy()
         assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), prec
+
+
+def test_transfers_full_size_properties(bench_setup):
+    """After the benchmark's setup, properties of the aggregation (Sec. 2.3) that hold at any size:
+    R P = I (P has orthonormal columns per aggregate half) and R Gamma5 = Gamma5_c R (P keeps the spin
+    chirality), in the FP32 arithmetic of the transfers."""
+    lib, ctx, _ = bench_setup
+    c = synth.gaussian_vectors(coarse_shape(), seed=7).cuda()
+    x = torch.zeros(DIMS[0], DIMS[3], DIMS[2], DIMS[1], 4, 3, dtype=torch.complex128, device="cuda")
+    lib.ddtm_prolong(ctx, 0, x, c, 1)
+    c2 = torch.zeros_like(c)
+    lib.ddtm_restrict(ctx, 0, c2, x, 1)
+    assert (torch.linalg.norm(c2 - c) / torch.linalg.norm(c)).item() <= 1e-4
+    f = synth.gaussian_spinor(DIMS, seed=8).cuda()
+    a, b = torch.zeros_like(c), torch.zeros_like(c)
+    lib.ddtm_restrict(ctx, 0, a, g5(f).contiguous(), 1)
+    lib.ddtm_restrict(ctx, 0, b, f, 1)
+    g5c = torch.cat([torch.ones(24), -torch.ones(24)]).to(torch.complex128).cuda()
+    assert (torch.linalg.norm(a - g5c * b) / torch.linalg.norm(b)).item() <= 1e-6
