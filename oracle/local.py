@@ -1,5 +1,6 @@
-"""Oracle: D(mu) psi evaluated at chosen sites only (Sec. 2.1), and one red-black SAP cycle (Sec. 2.4)
-evaluated at chosen blocks, for parity checks on lattices too large for a whole-lattice oracle run.
+"""Oracle: D(mu) psi evaluated at chosen sites only (Sec. 2.1), one red-black SAP cycle (Sec. 2.4) and
+the Galerkin coarse operator (Sec. 2.3) evaluated at chosen blocks, for parity checks on lattices too
+large for a whole-lattice oracle run.
 
 TEST INFRASTRUCTURE ONLY.  The operator is local: (D psi)(x) needs psi and the links within one hop of
 x, and the clover term at x needs the links of the four plaquette leaves around x in every plane.  Each
@@ -17,6 +18,7 @@ Arrays are (T, Z, Y, X, ...) as everywhere in the oracle; a site is given as (t,
 
 import numpy as np
 
+from . import aggregation
 from .dirac import gamma_matrices
 
 
@@ -179,3 +181,91 @@ def sap_cycle_at_block(U, kappa, c_sw, b, mu, bdims, bcoord, nmr, bc_t=0):
     r = spinors(sites, b) - apply_D_at_sites(U, kappa, c_sw, x, mu, sites, bc_t).reshape(-1)
     e = eo_block_mr(block_matrix(U, kappa, c_sw, mu, sites), r, sites, nmr)
     return e.reshape(len(sites), 4, 3)
+
+
+# ---- the Galerkin coarse operator (Sec. 2.3) at chosen aggregates -------------------------------------
+
+class _Aggregate:
+    """The lattice of one aggregate, for aggregation.build_P on that aggregate alone (the
+    orthonormalisation acts per aggregate half, so the result is that of the whole lattice there)."""
+
+    def __init__(self, lat):
+        self.lat = lat
+        self.dof = (4, 3)
+
+    def chirality_mask(self, s):
+        m = np.zeros(self.dof, dtype=bool)
+        m[2 * s:2 * s + 2, :] = True
+        return m
+
+
+def block_slices(bdims, bcoord):
+    """Array slices (t, z, y, x) of the block at bcoord in a (T, Z, Y, X, ...) field."""
+    o = [bcoord[k] * bdims[k] for k in range(4)]
+    return (slice(o[0], o[0] + bdims[0]), slice(o[3], o[3] + bdims[3]), slice(o[2], o[2] + bdims[2]),
+            slice(o[1], o[1] + bdims[1]))
+
+
+def prolongator_at_block(vb, bdims, bcoord):
+    """Columns of P on the aggregate at bcoord as a (12 Vb) x (2 Nv) matrix: rows in the order of
+    block_sites and spin-colour, columns (s, i) -> s Nv + i.  vb: the test vectors on the aggregate,
+    (Nv, bt, bz, by, bx, 4, 3) (a block_slices cut of the whole vectors)."""
+    t0, x0, y0, z0 = (bcoord[k] * bdims[k] for k in range(4))
+    W = aggregation.build_P(_Aggregate(vb.shape[1:5]), vb, bdims)  # (2, Nv, bt, bz, by, bx, 4, 3)
+    nv = vb.shape[0]
+    cols = []
+    for s in range(2):
+        for i in range(nv):
+            cols.append(np.concatenate([W[s, i, t - t0, z - z0, y - y0, x - x0].reshape(12)
+                                        for (t, x, y, z) in block_sites(bdims, bcoord)]))
+    return np.stack(cols, axis=1)
+
+
+def _coupling(U, rows, cols, bc_t, L):
+    """Hopping part of D from the sites `cols` to the sites `rows` (rows never equal cols): the hops
+    x -> x +- mu_hat with periodic wrap, a sign -1 on hops that wrap in t when bc_t = 1."""
+    g, _ = gamma_matrices()
+    i4 = np.eye(4)
+    index = {s: j for j, s in enumerate(cols)}
+    H = np.zeros((12 * len(rows), 12 * len(cols)), dtype=complex)
+    for i, s in enumerate(rows):
+        for d in range(4):
+            for sign in (1, -1):
+                n = list(s)
+                n[d] += sign
+                wraps = n[d] < 0 or n[d] >= L[d]
+                n[d] %= L[d]
+                j = index.get(tuple(n))
+                if j is None:
+                    continue
+                f = -1.0 if (wraps and d == 0 and bc_t == 1) else 1.0
+                if sign > 0:
+                    blk = np.kron(i4 - g[d], _link(U, L, s, d))
+                else:
+                    blk = np.kron(i4 + g[d], _link(U, L, n, d).conj().T)
+                H[12 * i:12 * i + 12, 12 * j:12 * j + 12] += -0.5 * f * blk
+    return H
+
+
+def coarse_columns_at_block(U, kappa, c_sw, v_at, mu, bdims, bcoord, bc_t=0):
+    """D_c(mu) e_(A, r) for the 2 Nv unit vectors of the coarse site A = bcoord, restricted to A and its
+    8 neighbouring coarse sites: {A: P_A^dagger (D + i mu Gamma5)_AA P_A,
+    B: P_B^dagger D_BA P_A for each neighbouring aggregate B}, each (2 Nv) x (2 Nv), column r for e_(A, r).
+    v_at(bc) returns the test vectors on the aggregate bc, (Nv, bt, bz, by, bx, 4, 3).  Every aggregate
+    lies inside the lattice (no wrap), so the self block needs no boundary phase; the couplings to
+    neighbours do (_coupling)."""
+    T, Z, Y, X = U.shape[:4]
+    L = (T, X, Y, Z)
+    NB = tuple(L[k] // bdims[k] for k in range(4))
+    sites_A = block_sites(bdims, bcoord)
+    P_A = prolongator_at_block(v_at(tuple(bcoord)), bdims, bcoord)
+    out = {tuple(bcoord): P_A.conj().T @ block_matrix(U, kappa, c_sw, mu, sites_A) @ P_A}
+    for d in range(4):
+        for sign in (1, -1):
+            bc = list(bcoord)
+            bc[d] = (bc[d] + sign) % NB[d]
+            bc = tuple(bc)
+            sites_B = block_sites(bdims, bc)
+            P_B = prolongator_at_block(v_at(bc), bdims, bc)
+            out[bc] = out.get(bc, 0) + P_B.conj().T @ _coupling(U, sites_B, sites_A, bc_t, L) @ P_A
+    return out

@@ -146,3 +146,50 @@ def test_transfers_full_size_properties(bench_setup):
     lib.ddtm_restrict(ctx, 0, b, f, 1)
     g5c = torch.cat([torch.ones(24), -torch.ones(24)]).to(torch.complex128).cuda()
     assert (torch.linalg.norm(a - g5c * b) / torch.linalg.norm(b)).item() <= 1e-6
+
+
+def test_coarse_operator_full_size_sampled_sites(full):
+    """The Galerkin coarse operator (Sec. 2.3) at full size, Nv = 24 seeded Gaussian test vectors on 4^4
+    aggregates (the benchmark's aggregation, without setup iterations): the columns D_c(mu) e_(A, r), all
+    48 of them, on A and its 8 neighbouring coarse sites, at a corner and an interior coarse site, against
+    the aggregate-local oracle (oracle/local.py), with FP32 SIMT and FP16 tensor-core coarse storage
+    within 1e-5 and 2e-3."""
+    lib, _, U = full
+    B, nv = (4, 4, 4, 4), 24
+    NB = (DIMS[0] // 4, DIMS[1] // 4, DIMS[2] // 4, DIMS[3] // 4)
+    sampled = [(0, 0, 0, 0), (7, 3, 5, 2)]
+    v = synth.gaussian_vectors((nv,) + (DIMS[0], DIMS[3], DIMS[2], DIMS[1], 4, 3), seed=9, device="cuda")
+    need = set()
+    for A in sampled:
+        need.add(A)
+        for d in range(4):
+            for s in (1, -1):
+                bc = list(A)
+                bc[d] = (bc[d] + s) % NB[d]
+                need.add(tuple(bc))
+    vb = {bc: v[(slice(None),) + local.block_slices(B, bc)].cpu().numpy() for bc in need}
+    want = {A: local.coarse_columns_at_block(U.numpy(), KAPPA, CSW, vb.__getitem__, MU, B, A) for A in sampled}
+    cshape = (NB[0], NB[3], NB[2], NB[1], 2 * nv)
+    for cprec, tol in ((lib.PREC_F32, 1e-5), (lib.PREC_F16, 2e-3)):
+        ctx = lib.ddtm_create(DIMS, B, 0)
+        try:
+            lib.ddtm_load_gauge(ctx, U.cuda(), KAPPA, CSW)
+            p = lib.ddtm_get_params(ctx)
+            p.nv[0] = nv
+            p.coarse_prec = cprec
+            lib.ddtm_set_params(ctx, p)
+            lib.ddtm_set_test_vectors(ctx, 0, v, nv)
+            for A in sampled:
+                x = torch.zeros((2 * nv,) + cshape, dtype=torch.complex128, device="cuda")
+                for r in range(2 * nv):
+                    x[r, A[0], A[3], A[2], A[1], r] = 1
+                y = torch.zeros_like(x)
+                lib.ddtm_apply_Dc(ctx, 1, y, x, 2 * nv, MU)
+                yh = y.cpu().numpy()
+                for bc, M in want[A].items():
+                    got = yh[:, bc[0], bc[3], bc[2], bc[1], :].T  # column r = rhs r
+                    assert np.linalg.norm(got - M) <= tol * np.linalg.norm(M), (cprec, A, bc)
+        finally:
+            lib.ddtm_destroy(ctx)
+    del v
+    torch.cuda.empty_cache()

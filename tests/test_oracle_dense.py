@@ -134,3 +134,31 @@ def test_sap_cycle_at_blocks_matches_the_whole_lattice_sap(bc_t):
         got = local.sap_cycle_at_block(U, kappa, csw, b, mu, B, bc, 3, bc_t)
         want = np.array([full[t, z, y, x] for (t, x, y, z) in local.block_sites(B, bc)])
         assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("bc_t", [0, 1])
+def test_galerkin_columns_at_blocks_match_the_whole_lattice_operator(bc_t):
+    """oracle/local.py's Galerkin operator at chosen aggregates (P per aggregate, dense block couplings,
+    for parity on lattices too large for the whole-lattice oracle) equals the columns D_c(mu) e_(A, r) of
+    the oracle's coarse operator on 8^4 with 2^4 aggregates (4 per direction, so the 8 neighbours are
+    distinct), at an interior and at a corner aggregate whose neighbours wrap around; D_c e_(A, r)
+    vanishes away from A and its neighbours."""
+    from oracle import aggregation, coarse, local
+    dims, B, nv, mu = (8, 8, 8, 8), (2, 2, 2, 2), 4, 0.05
+    U = synth.gauge_field(dims, 0.3, seed=3).numpy()
+    op = FineOperator(U, 0.13, 1.4, bc_t)
+    v = synth.gaussian_vectors((nv,) + op.lat + op.dof, seed=5).numpy()
+    cop = coarse.build_coarse_operator(op, aggregation.build_P(op, v, B), B)
+    for A in ((1, 2, 1, 2), (3, 0, 3, 0)):
+        cols = local.coarse_columns_at_block(U, 0.13, 1.4, lambda bc: v[(slice(None),) + local.block_slices(B, bc)],
+                                             mu, B, A, bc_t)
+        assert len(cols) == 9
+        for r in range(2 * nv):
+            e = np.zeros(cop.lat + cop.dof, dtype=complex)
+            e[A[0], A[3], A[2], A[1], r] = 1
+            y = cop.apply(e, mu)
+            scale = np.abs(y).max()
+            for bc, M in cols.items():
+                assert np.abs(M[:, r] - y[bc[0], bc[3], bc[2], bc[1]]).max() <= 1e-13 * scale
+                y[bc[0], bc[3], bc[2], bc[1]] = 0
+            assert np.abs(y).max() == 0
