@@ -153,7 +153,8 @@ def test_coarse_operator_full_size_sampled_sites(full):
     aggregates (the benchmark's aggregation, without setup iterations): the columns D_c(mu) e_(A, r), all
     48 of them, on A and its 8 neighbouring coarse sites, at a corner and an interior coarse site, against
     the aggregate-local oracle (oracle/local.py), with FP32 SIMT and FP16 tensor-core coarse storage
-    within 1e-5 and 2e-3."""
+    within 1e-5 and 2e-3; and R f = P^dagger f, P c at those aggregates (FP32 P from CGS2 with 24
+    vectors per aggregate half, 5e-6)."""
     lib, _, U = full
     B, nv = (4, 4, 4, 4), 24
     NB = (DIMS[0] // 4, DIMS[1] // 4, DIMS[2] // 4, DIMS[3] // 4)
@@ -179,6 +180,23 @@ def test_coarse_operator_full_size_sampled_sites(full):
             p.coarse_prec = cprec
             lib.ddtm_set_params(ctx, p)
             lib.ddtm_set_test_vectors(ctx, 0, v, nv)
+            if cprec == lib.PREC_F32:  # R = P^dagger and P at the sampled aggregates (FP32 transfers)
+                f = synth.gaussian_spinor(DIMS, seed=10)
+                c = synth.gaussian_vectors(cshape, seed=11)
+                rc = torch.zeros(cshape, dtype=torch.complex128, device="cuda")
+                lib.ddtm_restrict(ctx, 0, rc, f.cuda(), 1)
+                pf = torch.zeros_like(f).cuda()
+                lib.ddtm_prolong(ctx, 0, pf, c.cuda(), 1)
+                rc, pf = rc.cpu().numpy(), pf.cpu().numpy()
+                for A in sampled:
+                    PA = local.prolongator_at_block(vb[A], B, A)
+                    fA = np.concatenate([f.numpy()[t, z, y, x].reshape(12) for (t, x, y, z) in
+                                         local.block_sites(B, A)])
+                    want_r = PA.conj().T @ fA
+                    assert np.linalg.norm(rc[A[0], A[3], A[2], A[1]] - want_r) <= 5e-6 * np.linalg.norm(want_r)
+                    want_p = PA @ c.numpy()[A[0], A[3], A[2], A[1]]
+                    got_p = np.concatenate([pf[t, z, y, x].reshape(12) for (t, x, y, z) in local.block_sites(B, A)])
+                    assert np.linalg.norm(got_p - want_p) <= 5e-6 * np.linalg.norm(want_p)
             for A in sampled:
                 x = torch.zeros((2 * nv,) + cshape, dtype=torch.complex128, device="cuda")
                 for r in range(2 * nv):
