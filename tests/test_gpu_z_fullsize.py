@@ -1,4 +1,4 @@
-"""Parity at the benchmark's full size (32^3 x 64, the propagator workload of bench.py): D(mu) in FP64, FP32
+"""(Named to run after the other GPU test files.)  Parity at the benchmark's full size (32^3 x 64, the propagator workload of bench.py): D(mu) in FP64, FP32
 and FP16 storage at sampled sites against the site-local oracle (oracle/local.py), and properties that hold
 at any size on the library's own operators there: Gamma5-hermiticity of D(mu) in FP64 and of the
 tensor-core coarse operator built by the benchmark's setup."""
