@@ -1,7 +1,8 @@
-"""(Named to run after the other GPU test files.)  Parity at the benchmark's full size (32^3 x 64, the propagator workload of bench.py): D(mu) in FP64, FP32
-and FP16 storage at sampled sites against the site-local oracle (oracle/local.py), and properties that hold
-at any size on the library's own operators there: Gamma5-hermiticity of D(mu) in FP64 and of the
-tensor-core coarse operator built by the benchmark's setup."""
+"""Parity at the benchmark's full size (32^3 x 64, the propagator workload of bench.py), on outputs the
+oracle can compute piece by piece (oracle/local.py): D(mu) at sampled sites, one SAP cycle at sampled
+blocks, R, P and the Galerkin coarse operator at sampled aggregates; and properties that hold at any size:
+Gamma5-hermiticity of D(mu) and of the coarse operator after the benchmark's setup, R P = I and
+R Gamma5 = Gamma5_c R.  The file is named to run after the other GPU test files."""
 
 import numpy as np
 import pytest
