@@ -212,3 +212,28 @@ def test_coarse_operator_full_size_sampled_sites(full):
             lib.ddtm_destroy(ctx)
     del v
     torch.cuda.empty_cache()
+
+
+def test_sap_full_size_batched_12_rhs(full):
+    """The SAP cycle in the benchmark's launch configuration: 12 right-hand sides in one batch (one CTA per
+    block and right-hand side), FP16 storage, through the field API; the first and the last right-hand
+    side at a red and a black corner block against the block-local oracle within 2e-3."""
+    lib, ctx, U = full
+    B, nrhs = (4, 4, 4, 4), 12
+    b = synth.gaussian_spinor(DIMS, seed=12, nrhs=nrhs)
+    fb = lib.ddtm_field_create(ctx, lib.PREC_F16, nrhs)
+    fx = lib.ddtm_field_create(ctx, lib.PREC_F16, nrhs)
+    try:
+        lib.ddtm_field_import(ctx, fb, b.cuda())
+        lib.ddtm_sap_field(ctx, fx, fb, MU, 1, 3)
+        x = torch.zeros_like(b).cuda()
+        lib.ddtm_field_export(ctx, fx, x)
+        x = x.cpu().numpy()
+    finally:
+        lib.ddtm_field_destroy(fx)
+        lib.ddtm_field_destroy(fb)
+    for r in (0, nrhs - 1):
+        for c in ((15, 7, 7, 7), (1, 0, 0, 0)):
+            want = local.sap_cycle_at_block(U.numpy(), KAPPA, CSW, b[r].numpy(), MU, B, c, 3)
+            got = np.array([x[r, t, z, y, xx] for (t, xx, y, z) in local.block_sites(B, c)])
+            assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want), (r, c)
