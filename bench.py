@@ -290,12 +290,16 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+# at most this many oracle processes at once (each imports torch and holds its sample: ~1 GB)
+ORACLE_MAX_PROCS = 32
+
+
 def oracle_unit_times_all_cores(workload, ncores=None):
-    """oracle_unit_times in one single-threaded child process per host core, all running at once: each
-    child times the building blocks under full-node load, so the node does ncores units of work in the
-    time one child takes for one.  Returns the children's mean unit times divided by ncores (seconds per
+    """oracle_unit_times in one single-threaded child process per host core (at most ORACLE_MAX_PROCS), all
+    running at once: each child times the building blocks under full-node load, so the node does ncores
+    units of work in the time one child takes for one.  Returns the children's mean unit times divided by ncores (seconds per
     unit of work with every core busy) and ncores."""
-    ncores = ncores or host_cores()
+    ncores = ncores or min(host_cores(), ORACLE_MAX_PROCS)
     env = dict(os.environ, **ONE_THREAD)
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-units", workload]
     procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
