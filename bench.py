@@ -58,28 +58,38 @@ DSLASH_BYTES = {"f64": 1536, "f32": 768, "f16": 392}
 S2 = {"f64": 16, "f32": 8, "f16": 4}  # bytes per stored complex number
 
 
-def algorithmic_bytes(name, V, Vb, b, nv, Nc):
+def dslash_bytes(prec, nrhs):
+    """Algorithmic bytes per site of one D(mu) launch over nrhs right-hand sides: links (4 x 18 reals)
+    and clover (72 reals) once, x and y (24 reals each, + one 4-byte scale each in FP16) per rhs."""
+    s2 = S2[prec]
+    nrm = 4 if prec == "f16" else 0
+    return (36 + 36) * s2 + nrhs * 2 * (12 * s2 + nrm)
+
+
+def algorithmic_bytes(name, V, Vb, b, nv, Nc, rhs=1.0):
     """Algorithmic HBM bytes of one launch of kernel ``name`` (every array
-    element the kernel must touch, once), or None if no model applies."""
+    element the kernel must touch, once) carrying ``rhs`` right-hand sides, or
+    None if no model applies."""
     n = 2 * nv
     prec = name.rsplit("_", 1)[-1]
     s2 = S2.get(prec)
     face = sum(2.0 / bb for bb in b)  # halo sites per site of a block (both faces, 4 directions)
     if name.startswith("dslash_"):
-        return DSLASH_BYTES[prec] * V
+        return dslash_bytes(prec, rhs) * V
     if name.startswith("sap_half_"):
         half = V / 2
         nrm = 4 if prec == "f16" else 0
-        per = (36 + 36 + 36) * s2   # own links, clover, even-site inverses (72 complex per even site)
-        per += 12 * s2 + nrm        # b
-        per += 2 * (12 * s2 + nrm)  # x read and written on the block
-        per += face * (12 * s2 + nrm + 9 * s2 / 2)  # neighbour x on the faces, links of backward face hops
-        return half * per
+        per = (36 + 36 + 36) * s2   # own links, clover, even-site inverses (72 complex per even site): once
+        vec = 12 * s2 + nrm         # b
+        vec += 2 * (12 * s2 + nrm)  # x read and written on the block
+        vec += face * (12 * s2 + nrm)  # neighbour x on the faces
+        per += face * 9 * s2 / 2    # links of backward face hops
+        return half * (per + rhs * vec)
     if name.startswith("restrict_") or name.startswith("prolong_"):
         pbytes = 4 if (prec == "f16") else 8
         nrm = 4 if prec == "f16" else 0
         fine = V * (12 * s2 + nrm)
-        return V * 12 * nv * pbytes + fine * (2 if name.startswith("prolong") else 1) + Nc * n * 8
+        return V * 12 * nv * pbytes + rhs * (fine * (2 if name.startswith("prolong") else 1) + Nc * n * 8)
     if name.startswith("coarse_even_"):
         # 8 hop blocks and the FP32 self-block inverse per even site, read once per batch of NRHS
         d = S2[prec]
@@ -140,6 +150,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true", help="skip the oracle residual of the full-size solutions")
     ap.add_argument("--oracle-units", default=None, help=argparse.SUPPRESS)  # child process of the CPU baseline
     return ap.parse_args()
 
@@ -438,6 +449,10 @@ def main():
     Nc = V // Vb
     stream = torch.cuda.current_stream()
 
+    # measured SIMT arithmetic peaks of this device (FMA throughput, CUDA events), for the ALU rooflines
+    f32_peak, _, n_sm = ddtm.ddtm_measure_fma_peak(ddtm.PREC_F32)
+    f64_peak, _, _ = ddtm.ddtm_measure_fma_peak(ddtm.PREC_F64)
+
     ctx = ddtm.ddtm_create(dims, MG["block"], 0)
     ddtm.ddtm_set_stream(ctx, stream.cuda_stream)
     p = ddtm.ddtm_get_params(ctx)
@@ -469,9 +484,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---- headline: K steps, per-kernel timers off; the library counts its launches meanwhile
     clocks = ClockSampler(local)
+    ddtm.ddtm_timer_enable(ctx, False)
     ddtm.ddtm_timer_reset(ctx)
-    ddtm.ddtm_timer_enable(ctx, True)
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -481,27 +497,42 @@ def main():
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ddtm.ddtm_timer_enable(ctx, False)
-    counts = ddtm.ddtm_timer_report(ctx)
-    kernel_launches = ddtm.ddtm_timer_kernel_launches(ctx)
+    gpu_launches = ddtm.ddtm_timer_kernel_launches(ctx)  # every library kernel launched in the timed region
     ms = ev0.elapsed_time(ev1)
     t_step = ms / 1000.0 / args.steps
     t_step = max_over_ranks(t_step, dist, "cuda")
     value = t_step / world  # whole job: world propagators per step
+    x_timed = x.clone()
 
-    # residual check of the last solve with the library's FP64 operator
+    # ---- per-kernel breakdown: one more step of identical work with every launch bracketed by events
+    ddtm.ddtm_timer_reset(ctx)
+    ddtm.ddtm_timer_enable(ctx, True)
+    barrier()
+    ei0, ei1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ei0.record(stream)
+    step()
+    ei1.record(stream)
+    barrier()
+    ddtm.ddtm_timer_enable(ctx, False)
+    counts = ddtm.ddtm_timer_report(ctx)
+    instrumented_ms = ei0.elapsed_time(ei1)
+
+    # residual of the timed solutions with the library's FP64 operator
     r = torch.empty_like(x)
-    ddtm.ddtm_apply_D(ctx, r, x, NRHS, mu, ddtm.PREC_F64)
+    ddtm.ddtm_apply_D(ctx, r, x_timed, NRHS, mu, ddtm.PREC_F64)
     r = b - r
     relres = float(max((r[i].norm() / b[i].norm()).item() for i in range(NRHS)))
+    del r
 
-    # D(mu) stencil bandwidth on this lattice, L2 flushed between applications
+    # ---- D(mu) stencil on this lattice: 1 rhs per launch (FP16, FP32, FP64) and 12 rhs in one launch
+    # (FP16, FP32); inputs far above L2 and L2 flushed between applications
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
     dtm = {}
-    for prec, tag in ((ddtm.PREC_F16, "f16"), (ddtm.PREC_F32, "f32"), (ddtm.PREC_F64, "f64")):
-        fx = ddtm.ddtm_field_create(ctx, prec, 1)
-        fy = ddtm.ddtm_field_create(ctx, prec, 1)
-        ddtm.ddtm_field_import(ctx, fx, b[0].contiguous())
+    for prec, tag, nr in ((ddtm.PREC_F16, "f16", 1), (ddtm.PREC_F32, "f32", 1), (ddtm.PREC_F64, "f64", 1),
+                          (ddtm.PREC_F16, "f16", NRHS), (ddtm.PREC_F32, "f32", NRHS)):
+        fx = ddtm.ddtm_field_create(ctx, prec, nr)
+        fy = ddtm.ddtm_field_create(ctx, prec, nr)
+        ddtm.ddtm_field_import(ctx, fx, b[:nr].contiguous())
         times = []
         for it in range(13):
             flush.fill_(float(it))
@@ -513,7 +544,10 @@ def main():
             if it >= 3:
                 times.append(e0.elapsed_time(e1))
         tmed = statistics.median(times) / 1000.0
-        dtm[tag] = {"gbs": DSLASH_BYTES[tag] * V / tmed / 1e9, "ms": tmed * 1e3}
+        key = tag if nr == 1 else "%s_%drhs" % (tag, nr)
+        nbytes = dslash_bytes(tag, nr) * V
+        dtm[key] = {"gbs": nbytes / tmed / 1e9, "ms": tmed * 1e3, "bytes_per_launch": nbytes, "nrhs": nr,
+                    "tflops": 1920.0 * V * nr / tmed / 1e12}
         ddtm.ddtm_field_destroy(fx)
         ddtm.ddtm_field_destroy(fy)
     del flush
@@ -522,6 +556,11 @@ def main():
     hbm = peaks.get("hbm_gbs")
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
+    f32_tf, f64_tf = f32_peak / 1e12, f64_peak / 1e12
+
+    def rhs_per_launch(k):
+        v = counts[k]
+        return v.get("units", v["launches"]) / v["launches"]
 
     # algorithmic bytes per launch: stated by the library for the kernels that
     # know their operands (coarse passes, Krylov vectors), modelled here otherwise
@@ -529,50 +568,43 @@ def main():
         v = counts[k]
         if v.get("bytes"):
             return v["bytes"] / v["launches"]
-        return algorithmic_bytes(k, V, Vb, MG["block"], MG["nv"], Nc)
+        return algorithmic_bytes(k, V, Vb, MG["block"], MG["nv"], Nc, rhs_per_launch(k))
 
-    # dominant kernel of the step and its roofline
+    def flops_per_launch(k):
+        return algorithmic_flops(k, V, Vb, MG["block"], MG["nv"], MG["nmr"], rhs_per_launch(k))
+
+    # dominant kernel of the step and its roofline (durations from the instrumented step)
     kern = sorted(((v["ms"], k) for k, v in counts.items()), reverse=True)
     total_ms = sum(v["ms"] for v in counts.values())
     dom = kern[0][1]
     launches = counts[dom]["launches"]
     avg_s = counts[dom]["ms"] / launches / 1000.0
     nbytes = bytes_per_launch(dom)
-    def flops_per_launch(k):
-        v = counts[k]
-        return algorithmic_flops(k, V, Vb, MG["block"], MG["nv"], MG["nmr"],
-                                 v.get("units", v["launches"]) / v["launches"])
     fl = flops_per_launch(dom)
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes_per_site_rhs"] * (V / 2) * rhs_per_launch(dom) if tr else None
     if fl:
-        # FP32 SIMT arithmetic: 152 SMs x 128 FMA lanes x 2 flops at the sampled SM clock
-        alu = 152 * 128 * 2 * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
-        per_launch = fl
-        achieved = per_launch / avg_s / 1e12
-        tr = NCU_TRAFFIC.get(dom)
-        rpl = counts[dom].get("units", launches) / launches
-        traffic = tr["bytes_per_site_rhs"] * (V / 2) * rpl if tr else None
-        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
-                    "frac": achieved / alu, "traffic": traffic, "traffic_capture": tr["capture"] if tr else None,
-                    "share": counts[dom]["ms"] / total_ms,
-                    "launches_per_step": launches / args.steps, "flops_per_launch": per_launch,
-                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x sampled SM clock",
-                    "bytes_per_launch": nbytes}
+        achieved = fl / avg_s / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": f32_tf, "unit": "TFLOP/s",
+                    "frac": achieved / f32_tf, "traffic": traffic, "traffic_capture": tr["capture"] if tr else None,
+                    "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches,
+                    "flops_per_launch": fl, "bytes_per_launch": nbytes, "rhs_per_launch": rhs_per_launch(dom),
+                    "peak_source": "measured FP32 FMA throughput of this GPU (ddtm_measure_fma_peak, %d SMs)" % n_sm}
     else:
         achieved = nbytes / avg_s / 1e9 if nbytes else None
         roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm if achieved else None, "traffic": None,
-                    "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches / args.steps,
+                    "frac": achieved / hbm if achieved else None, "traffic": traffic,
+                    "share": counts[dom]["ms"] / total_ms, "launches_per_step": launches,
                     "bytes_per_launch": nbytes, "peak_source": peak_note}
+    roofline["durations"] = "per-launch CUDA events of one instrumented step of the same work after the timed region"
     breakdown = {}
     for k, v in sorted(counts.items(), key=lambda kv: -kv[1]["ms"]):
         nb = bytes_per_launch(k)
         fk = flops_per_launch(k)
-        breakdown[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                        "tflops": fk / (v["ms"] / v["launches"] / 1000.0) / 1e12 if fk else None,
-                        "units_per_step": v.get("units", v["launches"]) / args.steps,
-                        "share": v["ms"] / total_ms,
-                        "gbs": nb / (v["ms"] / v["launches"] / 1000.0) / 1e9 if nb else None}
-    gpu_launches = kernel_launches  # every library kernel launched in the timed region
+        t1 = v["ms"] / v["launches"] / 1000.0
+        breakdown[k] = {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
+                        "units_per_step": v.get("units", v["launches"]), "share": v["ms"] / total_ms,
+                        "gbs": nb / t1 / 1e9 if nb else None, "tflops": fk / t1 / 1e12 if fk else None}
 
     # end to end through host buffers: gauge upload + setup + solve with pinned host b and x
     e2e = None
@@ -581,7 +613,7 @@ def main():
         bh = b.cpu().pin_memory()
         xh = torch.zeros_like(bh).pin_memory()
         ts = []
-        for _ in range(args.steps):
+        for _ in range(min(args.steps, 3)):
             barrier()
             t0 = time.perf_counter()
             ddtm.ddtm_load_gauge(ctx, Uh, wl["kappa"], wl["c_sw"])
@@ -589,16 +621,27 @@ def main():
             info, code = ddtm.ddtm_solve(ctx, xh, bh, NRHS, mu)
             barrier()
             ts.append(time.perf_counter() - t0)
-        te = max_over_ranks(max(ts) if ts else float("nan"), dist, "cuda")
+        te = max_over_ranks(statistics.median(ts) if ts else float("nan"), dist, "cuda")
         e2e = {"value": te / world, "unit": UNIT, "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
-               "d2h_bytes_per_step": int(xh.numel() * 16)}
+               "d2h_bytes_per_step": int(xh.numel() * 16), "steps": len(ts)}
+        del Uh, bh, xh
 
+    # the mixed-precision solve driven to 1e-12 (the reference for the solution deviation below)
+    x_mix12 = None
+    if not args.no_fp64:
+        p12 = ddtm.ddtm_get_params(ctx)
+        p12.outer_tol = 1e-12
+        ddtm.ddtm_set_params(ctx, p12)
+        x_mix12 = torch.zeros_like(b)
+        ddtm.ddtm_solve(ctx, x_mix12, b, NRHS, mu)
     ddtm.ddtm_destroy(ctx)
 
-    # The plain FP64 method for comparison: FP64 outer FGMRES and SAP smoother,
-    # FP32 SIMT coarse operator, one right-hand side per solve.  One point
-    # source is solved and timed; 12 sequential solves cost 12 times that.
+    # The plain FP64 method for comparison (FP64 outer FGMRES and SAP smoother, FP32 SIMT coarse
+    # operator, one right-hand side per solve): one setup and the 12 point sources solved one after
+    # another, all timed.  Then the same method with its 12 solves driven to 1e-12, untimed: the
+    # mixed-precision solution at 1e-12 must agree with it within 1e-8.
     fp64 = None
+    deviation = None
     if not args.no_fp64:
         c64 = ddtm.ddtm_create(dims, MG["block"], 0)
         ddtm.ddtm_set_stream(c64, stream.cuda_stream)
@@ -610,38 +653,72 @@ def main():
         p.coarse_prec = ddtm.PREC_F32
         ddtm.ddtm_set_params(c64, p)
         ddtm.ddtm_load_gauge(c64, U, wl["kappa"], wl["c_sw"])
-        b1 = b[0:1].contiguous()
-        x1 = torch.zeros_like(b1)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        x64 = torch.zeros_like(b)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(NRHS + 2)]
+        iters, relres64, conv = [], [], True
         barrier()
-        e0.record(stream)
+        ev[0].record(stream)
         ddtm.ddtm_setup(c64, mu, SEED)
-        e1.record(stream)
-        info, code = ddtm.ddtm_solve(c64, x1, b1, 1, mu)
-        e2.record(stream)
+        ev[1].record(stream)
+        for i in range(NRHS):
+            info, code = ddtm.ddtm_solve(c64, x64[i], b[i], 1, mu)
+            ev[i + 2].record(stream)
+            iters.append(info.iters)
+            relres64.append(info.max_relres)
+            conv = conv and code == ddtm.OK
         barrier()
-        t_setup, t_solve = e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3
-        seq = t_setup + NRHS * t_solve
-        fp64 = {"setup_s": t_setup, "solve_s_one_rhs": t_solve, "iters": info.iters, "max_relres": info.max_relres,
-                "converged": code == ddtm.OK, "sequential_12_rhs_s": seq,
+        t_setup = ev[0].elapsed_time(ev[1]) / 1e3
+        t_solves = [ev[i + 1].elapsed_time(ev[i + 2]) / 1e3 for i in range(NRHS)]
+        seq = t_setup + sum(t_solves)
+        fp64 = {"setup_s": t_setup, "solve_s": t_solves, "iters": iters, "max_relres": max(relres64),
+                "converged": conv, "sequential_12_rhs_s": seq,
                 "speedup_mixed_batched_vs_fp64_sequential": seq / value,
                 "method": "FP64 outer FGMRES and SAP smoother, FP32 SIMT coarse stencil, one rhs per solve; "
-                          "one point source timed, 12 sequential solves = setup + 12 x that time"}
+                          "setup + the 12 point sources solved one after another, all timed with CUDA events"}
+        p.outer_tol = 1e-12
+        ddtm.ddtm_set_params(c64, p)
+        x64 = torch.zeros_like(b)
+        ddtm.ddtm_solve(c64, x64, b, NRHS, mu)  # the 12 sources in one batch of the plain FP64 method
         ddtm.ddtm_destroy(c64)
+        dev = [((x_mix12[i] - x64[i]).norm() / x64[i].norm()).item() for i in range(NRHS)]
+        deviation = {"max": max(dev), "per_rhs": dev,
+                     "method": "mixed-precision batched solve and the plain FP64 method, both to relative "
+                               "residual 1e-12; ||x_mixed - x_fp64|| / ||x_fp64|| per point source"}
+        del x64, x_mix12
+
+    # the timed solutions' residuals evaluated with the oracle's FP64 D on the host (slabs of t in a
+    # pool of spawned processes), independent of the library's operator
+    oracle_check = None
+    if rank == 0 and not args.no_oracle_check:
+        from oracle import slabs
+        t0 = time.perf_counter()
+        xs = x_timed.cpu().numpy()
+        bs = b.cpu().numpy()
+        rr = slabs.relative_residuals(U.cpu().numpy(), wl["kappa"], wl["c_sw"], bs, xs, mu, bc_t=0, slab=4,
+                                      workers=min(16, host_cores()))
+        oracle_check = {"max": max(rr), "per_rhs": rr, "s": time.perf_counter() - t0,
+                        "method": "oracle FP64 D (oracle/operators.py) evaluated per t-slab of 4 layers with a "
+                                  "halo of 1 (oracle/slabs.py) on the 12 solutions of the last timed step"}
+        del xs, bs
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         unit = oracle_unit_times_one_core(args.workload)
-        per_step_counts = {k: {"launches": v["launches"] / args.steps, "units": v.get("units", v["launches"]) / args.steps}
+        per_step_counts = {k: {"launches": v["launches"], "units": v.get("units", v["launches"])}
                            for k, v in counts.items()}
         est, _ = oracle_estimate(unit, per_step_counts, V, Nc)
         cpu = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+               "extrapolated": True,
                "sample": "oracle building blocks (D, SAP half-sweep, P, Galerkin, R, P, coarse even-odd GMRES "
                          "iteration) timed on a %s lattice with the same couplings and multigrid parameters, scaled "
                          "per site to %s and multiplied by this step's work units (right-hand sides and vectors "
-                         "processed per kernel family)" % (
+                         "processed per kernel family): an extrapolation, not a timing of the whole workload" % (
                              unit["_sample"], args.workload),
                "unit_s_per_site": {k: v for k, v in unit.items() if not k.startswith("_")}}
+        if oracle_check:
+            # measured at the workload's full size: the oracle's D on 12 right-hand sides, in parallel slabs
+            cpu["measured_full_size"] = {"oracle_D_12rhs_with_site_term_s": oracle_check["s"],
+                                         "processes": min(16, host_cores())}
         if not args.no_cpu_all:
             # the same oracle on every host core at once (one single-threaded process per core)
             try:
@@ -662,12 +739,23 @@ def main():
             "config": {"workload": "%s twisted-mass clover propagator, 12 point sources, two-level DD-alpha-AMG"
                                    % args.workload, "dims_TXYZ": list(dims), **{k: wl[k] for k in wl if k != "dims"},
                        "mg": MG, "nrhs": NRHS, "l2": "working set (test vectors, P, D_c) far above L2",
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "timers": "off in the timed region; per-kernel shares from one extra instrumented step"},
             "step": {"setup_s": info_last.get("setup_s"), "solve_s": info_last.get("solve_s"),
                      "outer_iters_max": info_last.get("iters"), "coarse_iters": info_last.get("coarse_iters"),
-                     "max_relres": relres},
+                     "max_relres": relres, "instrumented_step_ms": instrumented_ms},
+            "oracle_relres_max": oracle_check["max"] if oracle_check else None,
+            "oracle_relres": oracle_check,
+            "solution_deviation_max": deviation["max"] if deviation else None,
+            "solution_deviation": deviation,
             "dtm_apply": {"bound": "hbm", "peak": hbm, "unit": "GB/s",
-                          **{k: {"achieved": v["gbs"], "frac": v["gbs"] / hbm, "ms": v["ms"]} for k, v in dtm.items()}},
+                          "alu_peak_tflops": {"f32": f32_tf, "f64": f64_tf},
+                          **{k: {"achieved": v["gbs"], "frac": v["gbs"] / hbm, "ms": v["ms"], "nrhs": v["nrhs"],
+                                 "bytes_per_launch": v["bytes_per_launch"], "tflops": v["tflops"],
+                                 "alu_frac": v["tflops"] / (f64_tf if k == "f64" else f32_tf)}
+                             for k, v in dtm.items()}},
+            "peaks": {"f32_fma_tflops": f32_tf, "f64_fma_tflops": f64_tf, "sm_count": n_sm, "hbm_gbs": hbm,
+                      "hbm_source": peak_note},
             "roofline": roofline,
             "kernels": breakdown,
             "gpu_launches": gpu_launches,

@@ -229,7 +229,8 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
  * mu may be +mu or -mu with one setup (Sec. 3.1).  The right-hand sides are
  * solved in lockstep as one batch (every stencil, smoother and coarse-solve
  * launch covers all of them) unless their outer-solver fields do not fit in
- * the device memory, in which case they go in batches of the largest size that fits.  info
+ * the device memory (or exceed 256), in which case they go in batches of the largest size that fits
+ * (at most 256).  info
  * may be NULL.  DDTM_ERR_NOCONV (info still filled) if outer_max_iters is
  * exhausted; DDTM_ERR_TIMEOUT if a tensor-core pipeline wait gave up. */
 int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int loc,
@@ -254,6 +255,16 @@ int ddtm_timer_reset(ddtm_ctx* ctx);
  * counts timed launch scopes, u their work units (right-hand sides or vectors) and b their
  * algorithmic bytes where the library states them (0 otherwise). */
 int ddtm_timer_report(ddtm_ctx* ctx, char* buf, int len);
+
+/* Measured arithmetic peak of the current device's SIMT units: fused
+ * multiply-add throughput (2 flops each) in FP64 (prec = DDTM_PREC_F64) or
+ * FP32 (DDTM_PREC_F32), from a kernel of independent FMA chains on every SM,
+ * timed with CUDA events (best of four launches after two warm-ups) at the
+ * clocks the GPU runs at.  The roofline of the ALU-bound kernels is taken
+ * against it (the paper reports no device peaks).  *ms receives the best
+ * launch time and *sm_count the device's SM count (either may be NULL).
+ * DDTM_ERR_ARG for another prec; synchronises the device. */
+int ddtm_measure_fma_peak(int prec, double* flops_per_s, double* ms, int* sm_count);
 
 #ifdef __cplusplus
 }

@@ -102,9 +102,8 @@ float* field_nrm(const ddtm_field* f, int r) {
 
 void dslash_field(ddtm_ctx* c, ddtm_field* y, const ddtm_field* x, double mu) {
   ensure_fine_prec(c, x->prec);
-  for (int r = 0; r < x->nrhs; r++)
-    launch_dslash(c->g, x->prec, field_ptr(y, r), field_nrm(y, r), field_ptr(x, r), field_nrm(x, r),
-                  c->links[x->prec].p, c->clover[x->prec].p, mu, c->stream);
+  launch_dslash_multi(c->g, x->prec, field_ptr(y, 0), field_nrm(y, 0), field_ptr(x, 0), field_nrm(x, 0),
+                      c->links[x->prec].p, c->clover[x->prec].p, mu, x->nrhs, c->stream);
 }
 
 }  // namespace ddtm

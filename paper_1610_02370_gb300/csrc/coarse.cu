@@ -15,6 +15,7 @@
 #include "ddtm_internal.h"
 #include "timer.h"
 #include "coarse.h"
+#include "launch_shape.h"
 
 namespace ddtm {
 
@@ -304,6 +305,9 @@ __device__ __forceinline__ void load_rc(const cplx<float>* p, cplx<float> v[RC])
     float4 a = q[0], b = q[1];
     v[0] = cplx<float>(a.x, a.y); v[1] = cplx<float>(a.z, a.w);
     v[2] = cplx<float>(b.x, b.y); v[3] = cplx<float>(b.z, b.w);
+  } else if (RC == 2) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = cplx<float>(a.x, a.y); v[1] = cplx<float>(a.z, a.w);
   } else {
 #pragma unroll
     for (int c = 0; c < RC; c++) v[c] = p[c];
@@ -339,19 +343,23 @@ __device__ __forceinline__ void block_mv2(const DS* A, const cplx<float>* v, int
   }
 }
 
-// Threads of a site: n/2 row pairs x (R / RC) right-hand-side chunks, row pair
-// fastest (a warp reads consecutive 16-byte pieces of a column); SPB sites per CTA.
+// Threads of a site: n/2 row pairs x G chunk slots, row pair fastest (a warp
+// reads consecutive 16-byte pieces of a column); a thread takes the chunks
+// ch = g, g + G, ... of RC right-hand sides (launch_shape.h); SPB sites per CTA.
 template <typename DS, int RC>
 __global__ void __launch_bounds__(256) k_coarse_apply(cplx<float>* __restrict__ y, const cplx<float>* __restrict__ x_self,
                                                        const cplx<float>* __restrict__ x_hop, const DS* __restrict__ Dc,
                                                        const int* __restrict__ tab, const int* __restrict__ osite, int nout,
-                                                       int n, int nv, int R, float mu_c, int mode, float sres, float sy) {
-  const int np = n / 2, nch = R / RC, per = np * nch, spb = blockDim.x / per;
-  const int t = threadIdx.x, rp = t % np, ch = (t / np) % nch, q = t / per;
+                                                       int n, int nv, int R, int G, float mu_c, int mode, float sres,
+                                                       float sy) {
+  const int np = n / 2, nch = R / RC, per = np * G, spb = blockDim.x / per;
+  const int t = threadIdx.x, rp = t % np, g = (t / np) % G, q = t / per;
   const int idx = blockIdx.x * spb + q;
   if (q >= spb || idx >= nout) return;
   const int site = osite ? osite[idx] : idx;
-  const int r0 = 2 * rp, c0 = ch * RC;
+  const int r0 = 2 * rp;
+  for (int ch = g; ch < nch; ch += G) {
+  const int c0 = ch * RC;
   cplx<float> acc0[RC], acc1[RC];
 #pragma unroll
   for (int c = 0; c < RC; c++) acc0[c] = acc1[c] = cplx<float>(0, 0);
@@ -380,6 +388,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(cplx<float>* __restrict__ 
     yo0[c] = sy == 0.f ? res0 : sy * yo0[c] + res0;
     yo1[c] = sy == 0.f ? res1 : sy * yo1[c] + res1;
   }
+  }
 }
 
 // t[e] = Dinv_e (sr * rhs[e] + sh * hops(v)) on the even sites (compact even
@@ -390,15 +399,18 @@ template <typename DS, int RC>
 __global__ void __launch_bounds__(256) k_coarse_even(cplx<float>* __restrict__ t, const cplx<float>* __restrict__ rhs,
                                                       const cplx<float>* __restrict__ v, const DS* __restrict__ Dc,
                                                       const float2* __restrict__ Dinv, const int* __restrict__ tab,
-                                                      const int* __restrict__ even, int ne, int n, int R, float sr, float sh) {
+                                                      const int* __restrict__ even, int ne, int n, int R, int G, float sr,
+                                                      float sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int np = n / 2, nch = R / RC, per = np * nch, spb = blockDim.x / per;
+  const int np = n / 2, nch = R / RC, per = np * G, spb = blockDim.x / per;
   cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem_raw);  // [spb][n][R]
-  const int th = threadIdx.x, rp = th % np, ch = (th / np) % nch, q = th / per;
+  const int th = threadIdx.x, rp = th % np, g = (th / np) % G, q = th / per;
   const int e = blockIdx.x * spb + q;
   const bool act = q < spb && e < ne;
-  const int r0 = 2 * rp, c0 = ch * RC;
-  if (act) {
+  const int r0 = 2 * rp;
+  if (act)
+  for (int ch = g; ch < nch; ch += G) {
+    const int c0 = ch * RC;
     const int site = even[e];
     cplx<float> acc0[RC], acc1[RC];
 #pragma unroll
@@ -425,7 +437,9 @@ __global__ void __launch_bounds__(256) k_coarse_even(cplx<float>* __restrict__ t
     }
   }
   __syncthreads();
-  if (act) {
+  if (act)
+  for (int ch = g; ch < nch; ch += G) {
+    const int c0 = ch * RC;
     cplx<float> o0[RC], o1[RC];
 #pragma unroll
     for (int c = 0; c < RC; c++) o0[c] = o1[c] = cplx<float>(0, 0);
@@ -523,26 +537,24 @@ __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__
     }
 }
 
-// threads per CTA: whole sites of n * (R / RC) threads, at most 256 per CTA
-static int sites_per_cta(int per) { return per >= 256 ? 1 : 256 / per; }
-static int threads_per_site(int n, int R, int RC) { return n / 2 * (R / RC); }
-
 template <typename DS, int RC>
-static void coarse_apply_t(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
-                           const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  int per = threads_per_site(c.n, R, RC), spb = sites_per_cta(per);
-  unsigned grid = (unsigned)((nout + spb - 1) / spb);
+static void coarse_apply_t(const CoarseLevel& c, const CoarseShape& sh, cplx<float>* y, const cplx<float>* xs,
+                           const cplx<float>* xh, const int* tab, const int* osite, int nout, int R, double mu_c, int mode,
+                           float sres, float sy, cudaStream_t st) {
+  unsigned grid = (unsigned)((nout + sh.spb - 1) / sh.spb);
   if (grid == 0) return;
-  k_coarse_apply<DS, RC><<<grid, spb * per, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, R, (float)mu_c,
-                                                     mode, sres, sy);
+  k_coarse_apply<DS, RC><<<grid, sh.threads, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, R, sh.groups,
+                                                      (float)mu_c, mode, sres, sy);
   CKL("coarse_apply");
 }
 
 template <typename DS>
 static void coarse_apply_d(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
                            const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
-  if (R % 4 == 0) coarse_apply_t<DS, 4>(c, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
-  else coarse_apply_t<DS, 1>(c, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
+  const CoarseShape sh = coarse_shape(c.n, R);
+  if (sh.rc == 4) coarse_apply_t<DS, 4>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
+  else if (sh.rc == 2) coarse_apply_t<DS, 2>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
+  else coarse_apply_t<DS, 1>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
 }
 
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,
@@ -559,24 +571,27 @@ void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<
 }
 
 template <typename DS, int RC>
-static void coarse_even_t(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
-                          float sh, cudaStream_t st) {
-  int per = threads_per_site(c.n, R, RC), spb = sites_per_cta(per);
+static void coarse_even_t(const CoarseLevel& c, const CoarseShape& shp, cplx<float>* t, const cplx<float>* rhs,
+                          const cplx<float>* v, int R, float sr, float sh, cudaStream_t st) {
   int ne = (int)c.h_even.size();
-  unsigned grid = (unsigned)((ne + spb - 1) / spb);
+  unsigned grid = (unsigned)((ne + shp.spb - 1) / shp.spb);
   if (grid == 0) return;
-  size_t smem = (size_t)spb * c.n * R * sizeof(cplx<float>);
+  size_t smem = (size_t)shp.spb * c.n * R * sizeof(cplx<float>);
+  if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "coarse_even: " + std::to_string(R) + " right-hand sides of " +
+                                                       std::to_string(c.n) + " dofs exceed the shared-memory stage");
   set_dynamic_smem((const void*)k_coarse_even<DS, RC>, 200 * 1024);
-  k_coarse_even<DS, RC><<<grid, spb * per, smem, st>>>(t, rhs, v, c.Dc.as<DS>(), c.Dinv.as<float2>(), c.nbr_eo.as<int>(),
-                                                       c.even.as<int>(), ne, c.n, R, sr, sh);
+  k_coarse_even<DS, RC><<<grid, shp.threads, smem, st>>>(t, rhs, v, c.Dc.as<DS>(), c.Dinv.as<float2>(), c.nbr_eo.as<int>(),
+                                                         c.even.as<int>(), ne, c.n, R, shp.groups, sr, sh);
   CKL("coarse_even");
 }
 
 void launch_coarse_even(const CoarseLevel& c, cplx<float>* t, const cplx<float>* rhs, const cplx<float>* v, int R, float sr,
                         float sh, cudaStream_t st) {
   ScopedTimer timer_("coarse_even_f32", st, R);
-  if (R % 4 == 0) coarse_even_t<float2, 4>(c, t, rhs, v, R, sr, sh, st);
-  else coarse_even_t<float2, 1>(c, t, rhs, v, R, sr, sh, st);
+  const CoarseShape shp = coarse_shape(c.n, R);
+  if (shp.rc == 4) coarse_even_t<float2, 4>(c, shp, t, rhs, v, R, sr, sh, st);
+  else if (shp.rc == 2) coarse_even_t<float2, 2>(c, shp, t, rhs, v, R, sr, sh, st);
+  else coarse_even_t<float2, 1>(c, shp, t, rhs, v, R, sr, sh, st);
 }
 
 void launch_parity_copy(const CoarseLevel& c, int parity, cplx<float>* compact, cplx<float>* full, int R, int dir,

@@ -180,6 +180,9 @@ void launch_clover_build(const FineGeom& g, double* clov, const double* Ucanon, 
 void launch_site_inverse(const FineGeom& g, int prec, void* out, const double* clov64, double mu, cudaStream_t s);
 void launch_dslash(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
                    const void* links, const void* clover, double mu, cudaStream_t s);
+// nrhs right-hand sides at stride 12 V (FP16 scales at stride V), one launch where the block kernel applies
+void launch_dslash_multi(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
+                         const void* links, const void* clover, double mu, int nrhs, cudaStream_t s);
 
 // ---- sap.cu ----------------------------------------------------------------------
 void launch_sap_half(const FineGeom& g, int prec, void* x, float* xn, const void* b, const float* bn, const void* links,

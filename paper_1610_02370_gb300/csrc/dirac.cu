@@ -324,6 +324,95 @@ __global__ void __launch_bounds__(128) k_dslash(Spinor<P> y, Spinor<P> x, Links<
   y.store(blk, loc, out);
 }
 
+// ---- the stencil on whole lattice blocks -------------------------------------------------
+// One CTA per lattice block of VB sites (a compile-time size, so every
+// component offset inside the block is an immediate), one thread per site,
+// nrhs right-hand sides one after another.  For each right-hand side the
+// block's x is read once from HBM (coalesced, one component per warp load),
+// converted to FP32 with its per-site scale and staged in shared memory; the
+// hops that stay inside the block (3/4 of them for 4^4 blocks) read their
+// neighbour there, the hops that leave it read the neighbour block in global
+// memory.  Links and the clover term of the block are read through the
+// read-only cache with immediate offsets; with several right-hand sides the
+// CTA re-reads them from L1/L2, so HBM sees them once per launch.
+template <int P, int VB>
+__global__ void __launch_bounds__(VB, 3)
+    k_dslash_blk(Spinor<P> y, Spinor<P> x, Links<P> U, Clover<P> C, Geo g, float mu, int nrhs, size_t fstride,
+                 long V) {
+  typedef typename Prec<P>::store2 S;
+  __shared__ float2 xs[12 * VB];
+  const int blk = blockIdx.x, loc = threadIdx.x;
+  const S* ub = U.d + (size_t)blk * 36 * VB;
+  for (int r = 0; r < nrhs; r++) {
+    Spinor<P> xr = x, yr = y;
+    xr.d += (size_t)r * fstride;
+    yr.d += (size_t)r * fstride;
+    if (Prec<P>::scaled) {
+      xr.nrm += (size_t)r * V;
+      yr.nrm += (size_t)r * V;
+    }
+    {
+      cplx<float> in[12];
+      xr.load(blk, loc, in);
+#pragma unroll
+      for (int c = 0; c < 12; c++) xs[c * VB + loc] = make_float2(in[c].re, in[c].im);
+    }
+    __syncthreads();
+    cplx<float> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cplx<float>(0, 0);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int mu_ = k >> 1;
+      const bool fwd = (k & 1) == 0;
+      const uint32_t e = __ldg(g.loc_nbr + k * VB + loc);
+      const int nloc = e & 0xffff;
+      const bool cross = (e >> 16) & 1;
+      cplx<float> h[6], w[6], u[9];
+      int nblk = blk;
+      float sgn = 1.f;
+      {
+        cplx<float> p[12];
+        if (!cross) {
+#pragma unroll
+          for (int c = 0; c < 12; c++) {
+            float2 v = xs[c * VB + nloc];
+            p[c] = cplx<float>(v.x, v.y);
+          }
+        } else {
+          const int b = __ldg(g.blk_nbr + k * g.Nb + blk);
+          nblk = b & 0x3fffffff;
+          sgn = (b >> 30) & 1 ? -1.f : 1.f;
+          xr.load(nblk, nloc, p);
+        }
+        project<float>(mu_, fwd, p, h);
+      }
+      const S* ul = (fwd ? ub : U.d + (size_t)nblk * 36 * VB) + mu_ * 9 * VB + (fwd ? loc : nloc);
+#pragma unroll
+      for (int q = 0; q < 9; q++) u[q] = ld(ul + q * VB);
+      if (fwd) mul_U<float>(u, h, w);
+      else mul_Udag<float>(u, h, w);
+#pragma unroll
+      for (int q = 0; q < 6; q++) w[q] = sgn * w[q];
+      reconstruct<float>(mu_, fwd, w, acc);
+    }
+    cplx<float> in[12], out[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      float2 v = xs[c * VB + loc];
+      in[c] = cplx<float>(v.x, v.y);
+    }
+    C.apply(blk, loc, in, out);
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      const float m = c < 6 ? mu : -mu;
+      out[c] = out[c] + m * times_i(in[c]) + (-0.5f) * acc[c];
+    }
+    yr.store(blk, loc, out);
+    __syncthreads();  // xs is overwritten by the next right-hand side
+  }
+}
+
 static Geo make_geo(const FineGeom& g) {
   Geo q;
   q.Vb = g.Vb;
@@ -333,8 +422,43 @@ static Geo make_geo(const FineGeom& g) {
   return q;
 }
 
+// Block kernels exist for 4^4 blocks (VB = 256) in FP32 and FP16 storage.
+static bool dslash_blk_ok(const FineGeom& g, int prec) { return prec != PREC_F64 && g.Vb == 256; }
+
+template <int P>
+static void dslash_blk_t(const FineGeom& g, void* y, float* ynrm, const void* x, const float* xnrm, const void* links,
+                         const void* clover, double mu, int nrhs, cudaStream_t s) {
+  typedef typename Prec<P>::store2 S;
+  Spinor<P> Y{(S*)y, ynrm, g.Vb}, X{(S*)x, (float*)xnrm, g.Vb};
+  k_dslash_blk<P, 256><<<g.Nb, 256, 0, s>>>(Y, X, Links<P>{(const S*)links, g.Vb}, Clover<P>{(const S*)clover, g.Vb},
+                                             make_geo(g), (float)mu, nrhs, (size_t)g.V * 12, g.V);
+  CKL("dslash_blk");
+}
+
+// y = D(mu) x for nrhs right-hand sides at stride 12 V (store2 elements; FP16
+// scales at stride V): one launch for all of them with the block kernel, else
+// one launch per right-hand side.
+void launch_dslash_multi(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
+                         const void* links, const void* clover, double mu, int nrhs, cudaStream_t s) {
+  if (nrhs <= 0) return;
+  if (!dslash_blk_ok(g, prec)) {
+    const size_t fb = (size_t)g.V * 12 * (prec == PREC_F64 ? 16 : prec == PREC_F32 ? 8 : 4);
+    for (int r = 0; r < nrhs; r++)
+      launch_dslash(g, prec, (char*)y + r * fb, ynrm ? ynrm + (size_t)r * g.V : nullptr, (const char*)x + r * fb,
+                    xnrm ? xnrm + (size_t)r * g.V : nullptr, links, clover, mu, s);
+    return;
+  }
+  ScopedTimer timer_(prec == PREC_F32 ? "dslash_f32" : "dslash_f16", s, nrhs);
+  if (prec == PREC_F32) dslash_blk_t<PREC_F32>(g, y, ynrm, x, xnrm, links, clover, mu, nrhs, s);
+  else dslash_blk_t<PREC_F16>(g, y, ynrm, x, xnrm, links, clover, mu, nrhs, s);
+}
+
 void launch_dslash(const FineGeom& g, int prec, void* y, float* ynrm, const void* x, const float* xnrm,
                    const void* links, const void* clover, double mu, cudaStream_t s) {
+  if (dslash_blk_ok(g, prec)) {
+    launch_dslash_multi(g, prec, y, ynrm, x, xnrm, links, clover, mu, 1, s);
+    return;
+  }
   ScopedTimer timer_(prec == PREC_F64 ? "dslash_f64" : prec == PREC_F32 ? "dslash_f32" : "dslash_f16", s);
   Geo q = make_geo(g);
   unsigned grid = (unsigned)((g.V + 127) / 128);

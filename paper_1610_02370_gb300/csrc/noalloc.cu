@@ -10,6 +10,8 @@
 // device and kept by the GPU that loaded the library until the process exits.
 #include <string.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "solver.h"
@@ -22,12 +24,14 @@ using namespace ddtm;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // Device address of the array, looked up once per device with that device
-// current (in host code the symbol's name is only a host-side stand-in).
-static void* scratch_address() {
+// current (in host code the symbol's name is only a host-side stand-in).  The
+// per-device cache is guarded by a mutex, so host threads making their first
+// call at the same time do not race on it.
+static void* scratch_address(int dev) {
+  static std::mutex mtx;
   static void* addr[128] = {nullptr};
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 128) throw Error(DDTM_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(mtx);
   if (!addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -41,13 +45,18 @@ static void* scratch_address() {
   return addr[dev];
 }
 
-static bool is_device_pointer(const void* p) {
+// Device (or managed) memory of device dev; otherwise an error naming what was found.
+static void require_device_pointer(const void* p, int dev, const char* name) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    throw Error(DDTM_ERR_ARG, std::string(name) + " is not a CUDA pointer");
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    throw Error(DDTM_ERR_ARG, std::string(name) + " is not device memory (host or unregistered pointer)");
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    throw Error(DDTM_ERR_ARG, std::string(name) + " is memory of device " + std::to_string(a.device) +
+                                  ", the current device is " + std::to_string(dev));
 }
 
 extern "C" int ddtm_apply_D_noalloc(ddtm_ctx* ctx, double* y, const double* x, double mu, int prec) {
@@ -70,9 +79,11 @@ extern "C" int ddtm_apply_D_noalloc(ddtm_ctx* ctx, double* y, const double* x, d
     if (!ctx->links[prec].p || !ctx->clover[prec].p)
       throw Error(DDTM_ERR_STATE, "gauge field not yet held in this precision (one ddtm_apply_D call with it "
                                   "creates that copy); FP64 is always present");
-    if (!is_device_pointer(x) || !is_device_pointer(y))
-      throw Error(DDTM_ERR_ARG, "x and y must be device memory of the current device");
-    char* base = (char*)scratch_address();
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    require_device_pointer(x, dev, "x");
+    require_device_pointer(y, dev, "y");
+    char* base = (char*)scratch_address(dev);
     void* xi = base;
     float* xin = prec == PREC_F16 ? (float*)(base + field_al) : nullptr;
     void* yi = base + field_al + nrm_al;

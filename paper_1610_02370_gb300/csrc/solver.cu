@@ -75,9 +75,21 @@ void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const flo
 // ---- hierarchy -----------------------------------------------------------------------
 static size_t fine_field_bytes(const FineGeom& g, int prec) { return (size_t)g.V * 12 * store2_bytes(prec); }
 
-// coarse batches are padded to a multiple of 4 right-hand sides (register
-// blocking of the coarse kernels); the padding columns carry zeros
-int coarse_batch(int R) { return R == 1 ? 1 : (R + 3) / 4 * 4; }
+// coarse batches are padded with zero columns to a multiple of 4 right-hand
+// sides (register blocking of the coarse kernels) that the interleaved vector
+// kernels take: lcm(R, 32) <= 256, i.e. R / gcd(R, 32) <= 8 (so R <= 256)
+static bool interleave_ok(int R) {
+  int a = R, b = 32;
+  while (b) { int t = a % b; a = b; b = t; }
+  return R / a <= 8;
+}
+int coarse_batch(int R) {
+  if (R == 1) return 1;
+  int r = (R + 3) / 4 * 4;
+  while (r <= kMaxBatch && !interleave_ok(r)) r += 4;
+  if (r > kMaxBatch) throw Error(DDTM_ERR_ARG, "internal: coarse batch of " + std::to_string(R) + " right-hand sides");
+  return r;
+}
 
 // P from the current test vectors, then the Galerkin coarse operator
 void build_hierarchy(ddtm_ctx* c) {
@@ -414,10 +426,8 @@ OuterResult outer_fgmres(ddtm_ctx* c, double* x, const double* b, double mu, int
       launch_dslash(g, PREC_F64, out + 2 * (size_t)r * n, nullptr, in + 2 * (size_t)r * n, nullptr, c->links[0].p,
                     c->clover[0].p, mu, c->stream);
   };
-  auto Dcyc = [&](void* out, const void* in) {
-    for (int r = 0; r < R; r++)
-      launch_dslash(g, cp, (char*)out + (size_t)r * cb, nullptr, (const char*)in + (size_t)r * cb, nullptr,
-                    c->links[cp].p, c->clover[cp].p, mu, c->stream);
+  auto Dcyc = [&](void* out, const void* in) {  // all R right-hand sides in one launch where possible
+    launch_dslash_multi(g, cp, out, nullptr, in, nullptr, c->links[cp].p, c->clover[cp].p, mu, R, c->stream);
   };
   // device bookkeeping
   size_t nH = (size_t)R * (m + 1) * m, ncs = (size_t)R * m, ng = (size_t)R * (m + 1), nh = (size_t)(m + 1) * R;
@@ -879,6 +889,7 @@ static int solve_batch(ddtm_ctx* ctx, int nrhs) {
   const size_t avail = fr + held > reserve ? fr + held - reserve : 0;
   int R = per > 0 ? (int)(avail / per) : nrhs;
   if (R < 1) R = 1;
+  if (R > kMaxBatch) R = kMaxBatch;  // interleaved coarse batches hold at most kMaxBatch columns
   return R < nrhs ? R : nrhs;
 }
 

@@ -6,6 +6,10 @@
 
 namespace ddtm {
 
+// largest batch of right-hand sides one outer solve carries in lockstep (the
+// interleaved coarse vectors of a batch hold at most this many columns)
+static const int kMaxBatch = 256;
+
 size_t store2_bytes(int prec);
 void check_prec(int prec);
 void check_loc(int loc);

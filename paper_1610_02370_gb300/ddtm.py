@@ -79,6 +79,7 @@ SIGNATURES = {
     "ddtm_timer_enable": (_I, [_P, _I]),
     "ddtm_timer_reset": (_I, [_P]),
     "ddtm_timer_report": (_I, [_P, ctypes.c_char_p, _I]),
+    "ddtm_measure_fma_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
 }
 for _name, (_res, _args) in SIGNATURES.items():
     _f = getattr(_lib, _name)
@@ -298,3 +299,10 @@ def ddtm_timer_report(ctx):
 def ddtm_timer_kernel_launches(ctx):
     """Kernels the library launched since the last timer reset (timed or not)."""
     return int(_timer_json(ctx).get("_kernel_launches", 0))
+
+
+def ddtm_measure_fma_peak(prec):
+    """(flops per second, best launch ms, SM count) of the SIMT FMA units in FP64 or FP32."""
+    f, ms, sms = _D(0), _D(0), _I(0)
+    _check(None, _lib.ddtm_measure_fma_peak(prec, ctypes.byref(f), ctypes.byref(ms), ctypes.byref(sms)))
+    return f.value, ms.value, sms.value

@@ -2,7 +2,7 @@
 for timing and for profiling a single kernel in isolation.
 
     python -m paper_1610_02370_gb300.kernel_bench coarse --dims 48 24 24 24 --nv 24 --nrhs 12 --reps 4
-    python -m paper_1610_02370_gb300.kernel_bench dslash --dims 64 32 32 32 --prec 1 --reps 10
+    python -m paper_1610_02370_gb300.kernel_bench dslash --dims 64 32 32 32 --prec 1 --nrhs 1 --reps 10
     python -m paper_1610_02370_gb300.kernel_bench solve --dims 64 32 32 32 --nrhs 12 --outer-iters 1
     python -m paper_1610_02370_gb300.kernel_bench sap --dims 48 24 24 24 --nrhs 12 --cycles 2
 
@@ -132,12 +132,14 @@ def dslash(args):
     ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 0)
     try:
         ddtm.ddtm_load_gauge(ctx, U, args.kappa, args.csw)
-        x = synth.gaussian_spinor(dims, seed=1, device="cuda")
-        fx = ddtm.ddtm_field_create(ctx, args.prec, 1)
-        fy = ddtm.ddtm_field_create(ctx, args.prec, 1)
+        nr = args.nrhs if args.nrhs > 0 else 1
+        x = synth.gaussian_spinor(dims, seed=1, nrhs=nr, device="cuda")
+        fx = ddtm.ddtm_field_create(ctx, args.prec, nr)
+        fy = ddtm.ddtm_field_create(ctx, args.prec, nr)
         ddtm.ddtm_field_import(ctx, fx, x)
+        del x
         ms = _events(lambda: ddtm.ddtm_apply_D_field(ctx, fy, fx, 0.01), args.reps)
-        print(json.dumps({"kernel": "dslash", "dims": dims, "prec": args.prec, "ms_per_call": ms}))
+        print(json.dumps({"kernel": "dslash", "dims": dims, "prec": args.prec, "nrhs": nr, "ms_per_call": ms}))
         ddtm.ddtm_field_destroy(fx)
         ddtm.ddtm_field_destroy(fy)
     finally:

@@ -144,3 +144,37 @@ def test_errors_state_and_nan(lib):
         assert e.value.code == ddtm.ERR_ARG
     finally:
         ddtm.ddtm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_D_block_kernel_12_rhs_one_launch(lib, prec):
+    """The 4^4-block stencil with 12 right-hand sides in one launch (links and clover read once
+    per block for all of them), antiperiodic t: every right-hand side against the oracle, and
+    bit-equal to 12 single right-hand-side applications."""
+    ddtm = lib
+    dims, nrhs, mu = (16, 8, 8, 8), 12, 0.0015
+    U = synth.gauge_field(dims, 0.12, seed=7)
+    op = FineOperator(U.numpy(), 0.1372, 1.5755, 1)
+    x = synth.gaussian_spinor(dims, seed=8, nrhs=nrhs)
+    ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 1)
+    try:
+        ddtm.ddtm_load_gauge(ctx, U.cuda(), 0.1372, 1.5755)
+        fx = ddtm.ddtm_field_create(ctx, prec, nrhs)
+        fy = ddtm.ddtm_field_create(ctx, prec, nrhs)
+        ddtm.ddtm_field_import(ctx, fx, x.cuda())
+        ddtm.ddtm_apply_D_field(ctx, fy, fx, mu)
+        y = torch.zeros_like(x).cuda()
+        ddtm.ddtm_field_export(ctx, fy, y)
+        ddtm.ddtm_field_destroy(fx)
+        ddtm.ddtm_field_destroy(fy)
+        y1 = torch.zeros_like(x).cuda()
+        for r in range(nrhs):
+            ddtm.ddtm_apply_D(ctx, y1[r], x[r].cuda(), 1, mu, prec)
+        torch.cuda.synchronize()
+        assert torch.equal(y, y1)
+        y = y.cpu().numpy()
+        for r in range(nrhs):
+            e = relerr(y[r], op.apply(x[r].numpy(), mu))
+            assert e < TOL[prec], (prec, r, e)
+    finally:
+        ddtm.ddtm_destroy(ctx)

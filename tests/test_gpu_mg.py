@@ -234,3 +234,52 @@ def test_setup_invariants_and_save_load(lib, tmp_path):
     finally:
         lib.ddtm_destroy(ctx)
         lib.ddtm_destroy(ctx2)
+
+
+@pytest.fixture(scope="module")
+def case24(lib):
+    """8^4 lattice, 4^4 aggregates, N_v = 24 (n = 48 dofs per coarse site, the workload's coarse
+    block size): FP32 and FP16 coarse storage from the same test vectors."""
+    c32 = Case(lib, (8, 8, 8, 8), (4, 4, 4, 4), 0.3, 0.13, 1.2, 24, lib.PREC_F32, seed=4)
+    c16 = Case(lib, (8, 8, 8, 8), (4, 4, 4, 4), 0.3, 0.13, 1.2, 24, lib.PREC_F16, seed=4)
+    yield c32, c16
+    lib.ddtm_destroy(c32.ctx)
+    lib.ddtm_destroy(c16.ctx)
+
+
+@pytest.mark.parametrize("nrhs", [11, 13, 44, 48])
+@pytest.mark.parametrize("which", ["f32", "f16"])
+def test_coarse_operator_ragged_batches_nv24(lib, case24, nrhs, which):
+    """D_c (Sec. 2.3) on batches whose thread shape once exceeded a CTA (n = 48 with 11, 13, 44
+    or 48 right-hand sides): every column against the oracle's Galerkin operator."""
+    c = case24[0] if which == "f32" else case24[1]
+    tol = 1e-5 if which == "f32" else 2e-3
+    cl = c.cop.lat
+    x = synth.gaussian_vectors((nrhs,) + cl + (2 * c.nv,), seed=40 + nrhs)
+    y = torch.zeros_like(x).cuda()
+    lib.ddtm_apply_Dc(c.ctx, 1, y, x.cuda(), nrhs, 0.02)
+    y = y.cpu().numpy()
+    for r in range(nrhs):
+        want = c.cop.apply(x[r].numpy(), 0.02)
+        assert relerr(y[r], want) < tol, (r, relerr(y[r], want))
+
+
+def test_solve_fp32_coarse_many_rhs(lib):
+    """A 44-rhs batch with the FP32 SIMT coarse stencil (the coarse batch of 44 right-hand sides
+    goes through the even-odd coarse kernels in one launch): every solve to 1e-10."""
+    dims, block, nv, mu = (8, 8, 8, 8), (4, 4, 4, 4), 24, 0.01
+    U = synth.gauge_field(dims, 0.3, seed=0)
+    op = FineOperator(U.numpy(), 0.13, 1.2)
+    ctx = make_ctx(lib, dims, block, U, 0.13, 1.2, nv, n_setup=2, coarse_prec=lib.PREC_F32, post_smooth=2)
+    try:
+        lib.ddtm_setup(ctx, mu, 99)
+        b = synth.gaussian_spinor(dims, seed=8, nrhs=44)
+        x = torch.zeros_like(b).cuda()
+        info, code = lib.ddtm_solve(ctx, x, b.cuda(), 44, mu)
+        assert code == lib.OK, lib.ddtm_last_error(ctx)
+        xh = x.cpu().numpy()
+        for r in range(44):
+            rel = np.linalg.norm(b[r].numpy() - op.apply(xh[r], mu)) / np.linalg.norm(b[r].numpy())
+            assert rel <= 1e-10, (r, rel)
+    finally:
+        lib.ddtm_destroy(ctx)

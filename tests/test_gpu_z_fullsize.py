@@ -237,3 +237,46 @@ def test_sap_full_size_batched_12_rhs(full):
             want = local.sap_cycle_at_block(U.numpy(), KAPPA, CSW, b[r].numpy(), MU, B, c, 3)
             got = np.array([x[r, t, z, y, xx] for (t, xx, y, z) in local.block_sites(B, c)])
             assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want), (r, c)
+
+
+def test_propagator_full_size_oracle_residual_and_deviation(bench_setup):
+    """The benchmark's propagator at full size: the 12 point sources solved in one mixed-precision batch
+    to 1e-10 (Sec. 2.5 outer FGMRES stopping rule), each residual evaluated with the oracle's FP64 D
+    (whole lattice, per t-slab, oracle/slabs.py) <= 1e-10; then the same batch driven to 1e-12 against
+    the plain FP64 method driven to 1e-12: solutions within 1e-8 (the bound kappa(D) (tol_a + tol_b)
+    allows with sigma_min >= mu)."""
+    from oracle import slabs
+    lib, ctx, U = bench_setup
+    b = synth.point_sources(DIMS, device="cuda")
+    x = torch.zeros_like(b)
+    info, code = lib.ddtm_solve(ctx, x, b, 12, MU)
+    assert code == lib.OK, lib.ddtm_last_error(ctx)
+    rr = slabs.relative_residuals(U.numpy(), KAPPA, CSW, b.cpu().numpy(), x.cpu().numpy(), MU, bc_t=0, slab=4,
+                                  workers=16)
+    assert max(rr) <= 1e-10, rr
+    p = lib.ddtm_get_params(ctx)
+    tol0 = p.outer_tol
+    p.outer_tol = 1e-12
+    lib.ddtm_set_params(ctx, p)
+    try:
+        xm = torch.zeros_like(b)
+        info, code = lib.ddtm_solve(ctx, xm, b, 12, MU)
+        assert code == lib.OK, lib.ddtm_last_error(ctx)
+    finally:
+        p.outer_tol = tol0
+        lib.ddtm_set_params(ctx, p)
+    c64 = lib.ddtm_create(DIMS, (4, 4, 4, 4), 0)
+    try:
+        lib.ddtm_load_gauge(c64, U.cuda(), KAPPA, CSW)
+        q = lib.ddtm_get_params(c64)
+        q.nv[0], q.n_setup, q.post_smooth, q.outer_tol = 24, 6, 2, 1e-12
+        q.smoother_prec, q.coarse_prec = lib.PREC_F64, lib.PREC_F32
+        lib.ddtm_set_params(c64, q)
+        lib.ddtm_setup(c64, MU, 2024)
+        x64 = torch.zeros_like(b)
+        info, code = lib.ddtm_solve(c64, x64, b, 12, MU)
+        assert code == lib.OK, lib.ddtm_last_error(c64)
+    finally:
+        lib.ddtm_destroy(c64)
+    dev = [((xm[i] - x64[i]).norm() / x64[i].norm()).item() for i in range(12)]
+    assert max(dev) <= 1e-8, dev

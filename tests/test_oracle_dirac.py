@@ -313,3 +313,20 @@ def test_synthetic_links_are_su3():
     want = Vv @ np.diag(np.exp(1j * 0.8 * w)) @ Vv.conj().T
     got = synth.expm_i_hermitian(torch.from_numpy(H)[None], 0.8).numpy()[0]
     assert np.max(np.abs(got - want)) < 1e-14
+
+
+@pytest.mark.parametrize("bc_t", [0, 1])
+def test_slab_decomposed_D_equals_whole_lattice(bc_t):
+    """oracle/slabs.py: D evaluated per t-slab with a halo of one layer reproduces the whole-lattice
+    oracle D (the clover term included), both time boundary conditions, in-process and in a pool."""
+    from oracle import slabs
+    from oracle.operators import FineOperator
+    dims = (12, 4, 6, 4)
+    U = synth.gauge_field(dims, 0.4, seed=21).numpy()
+    op = FineOperator(U, 0.13, 1.7, bc_t)
+    psis = [synth.gaussian_spinor(dims, seed=22 + r).numpy() for r in range(2)]
+    want = [op.apply(p, 0.07) for p in psis]
+    for workers, slab in ((0, 3), (2, 4)):
+        got = slabs.apply_D_slabs(U, 0.13, 1.7, psis, 0.07, bc_t, slab=slab, workers=workers)
+        for g, w in zip(got, want):
+            assert np.max(np.abs(g - w)) <= 1e-13 * np.max(np.abs(w))
