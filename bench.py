@@ -151,6 +151,9 @@ def parse_args():
     ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the oracle residual of the full-size solutions")
+    ap.add_argument("--study", choices=["eo-cg", "aggregation"], default=None,
+                    help="eo-cg: the even-odd CG baseline against DD-alpha-AMG, t_total = t_setup + n_rhs t_solve "
+                         "(Sec. 3.1.2, Fig. 3); aggregation: block size x N_v sweep (Sec. 3.3, Table 4)")
     ap.add_argument("--oracle-units", default=None, help=argparse.SUPPRESS)  # child process of the CPU baseline
     return ap.parse_args()
 
@@ -412,6 +415,93 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+# ---- studies (one GPU, not part of the benchmark line) -------------------------------------------
+def _mg_ctx(ddtm, dims, U, wl, block=None, nv=None, stream=None):
+    ctx = ddtm.ddtm_create(dims, block or MG["block"], 0)
+    if stream is not None:
+        ddtm.ddtm_set_stream(ctx, stream.cuda_stream)
+    p = ddtm.ddtm_get_params(ctx)
+    p.nv[0] = nv or MG["nv"]
+    for k in ("n_setup", "post_smooth", "nmr", "outer_restart", "outer_tol", "smoother_prec", "coarse_prec"):
+        setattr(p, k, MG[k])
+    ddtm.ddtm_set_params(ctx, p)
+    ddtm.ddtm_load_gauge(ctx, U, wl["kappa"], wl["c_sw"])
+    return ctx
+
+
+def _timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def study(args):
+    import torch
+    from paper_1610_02370_gb300 import build as _build
+    _build.build()
+    from paper_1610_02370_gb300 import ddtm, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = WORKLOADS[args.workload]
+    dims = wl["dims"]
+    mu = wl["mu"]
+    U = synth.gauge_field(dims, wl["eps"], seed=0, device="cuda")
+    b = synth.point_sources(dims, device="cuda")
+    out = {"study": args.study, "workload": args.workload, "mu": mu}
+    if args.study == "eo-cg":
+        # DD-alpha-AMG: one setup, then the 12 point sources in one batch (warm-up run first)
+        ctx = _mg_ctx(ddtm, dims, U, wl, stream=stream)
+        x = torch.zeros_like(b)
+        ddtm.ddtm_setup(ctx, mu, SEED)
+        ddtm.ddtm_solve(ctx, x, b, NRHS, mu)
+        t_setup, _ = _timed(torch, stream, lambda: ddtm.ddtm_setup(ctx, mu, SEED))
+        t_solve12, (info, code) = _timed(torch, stream, lambda: ddtm.ddtm_solve(ctx, x, b, NRHS, mu))
+        ddtm.ddtm_destroy(ctx)
+        # even-odd CG (FP64), one point source, to the same true relative residual
+        c2 = ddtm.ddtm_create(dims, MG["block"], 0)
+        ddtm.ddtm_set_stream(c2, stream.cuda_stream)
+        ddtm.ddtm_load_gauge(c2, U, wl["kappa"], wl["c_sw"])
+        x1 = torch.zeros_like(b[0])
+        t_cg, (cinfo, ccode) = _timed(torch, stream,
+                                      lambda: ddtm.ddtm_eo_cg(c2, x1, b[0], 1, mu, MG["outer_tol"], 200000))
+        ddtm.ddtm_destroy(c2)
+        t_rhs = t_solve12 / NRHS
+        out.update({"mg": {"setup_s": t_setup, "solve_12rhs_s": t_solve12, "solve_per_rhs_s": t_rhs,
+                           "outer_iters": info.iters, "max_relres": info.max_relres},
+                    "eo_cg": {"solve_s": t_cg, "iters": cinfo.iters, "relres": cinfo.max_relres,
+                              "converged": ccode == ddtm.OK, "s_per_iter": t_cg / max(cinfo.iters, 1)},
+                    "t_total_s": {str(n): {"mg": t_setup + n * t_rhs, "eo_cg": n * t_cg,
+                                           "speedup": n * t_cg / (t_setup + n * t_rhs)} for n in (1, 12, 100)},
+                    "model": "t_total(n) = t_setup + n t_solve (MG, solve per rhs from the 12-rhs batch) "
+                             "against n t_cg (one CG solve per rhs)"})
+    else:
+        runs = []
+        for block in ((4, 4, 4, 4), (2, 2, 2, 2)):
+            for nv in (16, 24, 32):
+                ctx = _mg_ctx(ddtm, dims, U, wl, block=block, nv=nv, stream=stream)
+                x = torch.zeros_like(b)
+                try:
+                    ddtm.ddtm_setup(ctx, mu, SEED)
+                    ddtm.ddtm_solve(ctx, x, b, NRHS, mu)
+                    t_setup, _ = _timed(torch, stream, lambda: ddtm.ddtm_setup(ctx, mu, SEED))
+                    t_solve, (info, code) = _timed(torch, stream, lambda: ddtm.ddtm_solve(ctx, x, b, NRHS, mu))
+                    runs.append({"block": block, "nv": nv, "setup_s": t_setup, "solve_s": t_solve,
+                                 "total_s": t_setup + t_solve, "outer_iters": info.iters,
+                                 "coarse_rhs_iters": info.coarse_iters, "max_relres": info.max_relres,
+                                 "converged": code == ddtm.OK})
+                except ddtm.DDTMError as e:
+                    runs.append({"block": block, "nv": nv, "error": str(e)[:200]})
+                finally:
+                    ddtm.ddtm_destroy(ctx)
+                torch.cuda.empty_cache()
+        out["runs"] = runs
+    print(json.dumps(out))
+
+
 # ---- our arm ------------------------------------------------------------------------------------
 def main():
     args = parse_args()
@@ -420,6 +510,9 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.study:
+        study(args)
         return
     import numpy as np
     import torch

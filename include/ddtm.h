@@ -38,6 +38,7 @@
 #ifndef DDTM_H
 #define DDTM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -236,10 +237,60 @@ int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, in
 int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, int loc,
                ddtm_solve_info* info);
 
+/* The baseline solver the paper compares with (Sec. 3.1.2): conjugate
+ * gradient on the normal equations D_hat^+ D_hat x_o = D_hat^+ rhat of the
+ * even-odd Schur complement D_hat = D_oo - D_oe D_ee^-1 D_eo (odd sites; the
+ * even sites follow by D_ee^-1), in FP64 on the GPU, one right-hand side
+ * after another; needs only the gauge field (no setup).  D_hat^+ is applied
+ * as Gamma5 D_hat(-mu) Gamma5.  Each solve stops when the true FP64 relative
+ * residual ||b - D(mu) x|| / ||b|| is <= tol (checked after the residual of the
+ * normal equations has dropped by tol, and again while it is not) or after
+ * max_iter CG iterations (DDTM_ERR_NOCONV, info still filled).  info: iters =
+ * CG iterations (max over right-hand sides), max_relres, solve_s. */
+int ddtm_eo_cg(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, double tol, int max_iter, int loc,
+               ddtm_solve_info* info);
+
 /* Save / load the setup (parameters, mu, test vectors of every level) to a
  * file; loading rebuilds P and the coarse operators. */
 int ddtm_save_setup(ddtm_ctx* ctx, const char* path);
 int ddtm_load_setup(ddtm_ctx* ctx, const char* path);
+
+/* ---- execution options ---------------------------------------------------------- */
+
+/* Set / read an execution option of the context (results do not depend on it):
+ *   "graphs" (default 1): each iteration of the coarsest even-odd GMRES
+ *     (Sec. 2.5; operator passes, Gram-Schmidt, Givens update, residual
+ *     estimate) is captured once per iteration index, batch and buffer set
+ *     into a CUDA graph and replayed with one launch; 0 launches its kernels
+ *     one by one.  Graphs are not used while the per-kernel timers are on.
+ *   "graphs_cached" (read only): executable graphs held by the context.
+ *   "autotune" (default 1, process-wide): the first launch of each shape of
+ *     the tensor-core coarse stencil pass (column groups, rows, outputs)
+ *     outside stream capture times every residency its registers allow (1, 2
+ *     or 3 CTAs per SM, the stage ring filling the shared memory left per CTA)
+ *     and keeps the fastest for that shape; each output is formed by the same
+ *     MMAs in the same order in every variant, so results do not change.
+ *     0 uses the fixed rule (2 CTAs per SM up to 16 right-hand sides, else 1).
+ * DDTM_ERR_ARG for an unknown name. */
+int ddtm_set_option(ddtm_ctx* ctx, const char* name, int value);
+int ddtm_get_option(ddtm_ctx* ctx, const char* name, int* value);
+/* The autotuner's choices so far as a JSON object (NUL-terminated, truncated
+ * to len): {"<pass>|n<rows>|R<rhs>|out<outputs>|s<self>|h<hops>":
+ * {"ctas_per_sm": k, "ms": [time with 1, 2, ... CTAs per SM]}, ...}. */
+int ddtm_autotune_report(char* buf, int len);
+
+/* ---- device memory budget ---------------------------------------------------- */
+
+/* Cap on the device memory the library holds, over all contexts of the
+ * process (bytes; 0 removes the cap, the default).  An allocation that would
+ * exceed it fails with DDTM_ERR_OOM before cudaMalloc is called, exactly as a
+ * failed cudaMalloc does; the call that needed it returns DDTM_ERR_OOM and the
+ * context stays usable (a later call may succeed under a larger cap).  Lets a
+ * caller that shares the GPU keep the solver within a share of HBM (the paper
+ * has no counterpart; it runs one solver per node). */
+int ddtm_set_memory_limit(size_t bytes);
+/* Device bytes the library holds now (all contexts and fields). */
+int ddtm_memory_in_use(size_t* bytes);
 
 /* ---- measurement ------------------------------------------------------------ */
 

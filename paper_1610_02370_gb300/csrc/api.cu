@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "coarse.h"
 #include "solver.h"
 #include "timer.h"
 
@@ -131,6 +132,9 @@ void ddtm_ctx::events(const std::string& name, cudaEvent_t ev[2]) {
 }
 
 ddtm_ctx::~ddtm_ctx() {
+  for (auto& kv : graphs)
+    if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+  if (capture_stream) cudaStreamDestroy(capture_stream);
   for (auto& kv : host_bufs) cudaFreeHost(kv.second.first);
   for (auto& kv : event_pairs) {
     cudaEventDestroy(kv.second.first);
@@ -344,6 +348,54 @@ int ddtm_apply_D_field(ddtm_ctx* ctx, ddtm_field* y, const ddtm_field* x, double
     throw Error(DDTM_ERR_ARG, "fields must differ and share context, precision and nrhs");
   dslash_field(ctx, y, x, mu);
   API_END(ctx)
+}
+
+int ddtm_set_option(ddtm_ctx* ctx, const char* name, int value) {
+  API_BEGIN(ctx)
+  if (!name) throw Error(DDTM_ERR_ARG, "null option name");
+  const std::string n(name);
+  if (n == "graphs") {
+    ctx->use_graphs = value != 0;
+  } else if (n == "autotune") {
+    tc_autotune_enable(value != 0);
+  } else {
+    throw Error(DDTM_ERR_ARG, "unknown option " + n);
+  }
+  API_END(ctx)
+}
+
+int ddtm_get_option(ddtm_ctx* ctx, const char* name, int* value) {
+  API_BEGIN(ctx)
+  if (!name || !value) throw Error(DDTM_ERR_ARG, "null argument");
+  const std::string n(name);
+  if (n == "graphs") *value = ctx->use_graphs ? 1 : 0;
+  else if (n == "graphs_cached") *value = (int)ctx->graphs.size();
+  else throw Error(DDTM_ERR_ARG, "unknown option " + n);
+  API_END(ctx)
+}
+
+int ddtm_autotune_report(char* buf, int len) {
+  if (!buf || len <= 0) return DDTM_ERR_ARG;
+  try {
+    const std::string s = tc_autotune_report();
+    const size_t n = s.size() < (size_t)len - 1 ? s.size() : (size_t)len - 1;
+    memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  } catch (const std::exception&) {
+    return DDTM_ERR_CUDA;
+  }
+  return DDTM_OK;
+}
+
+int ddtm_set_memory_limit(size_t bytes) {
+  set_device_memory_limit(bytes);
+  return DDTM_OK;
+}
+
+int ddtm_memory_in_use(size_t* bytes) {
+  if (!bytes) return DDTM_ERR_ARG;
+  *bytes = device_bytes_in_use();
+  return DDTM_OK;
 }
 
 int ddtm_timer_enable(ddtm_ctx* ctx, int on) {

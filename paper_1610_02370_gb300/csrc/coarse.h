@@ -1,6 +1,8 @@
 // Host interface of the aggregation and coarse-level kernels (transfer.cu, coarse.cu).
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 #include "ddtm_internal.h"
 
@@ -81,6 +83,10 @@ struct TcPass {
   void* yt = nullptr;
 };
 void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t st);
+// autotuner of the tensor-core pass residency (process-wide): switch, and the
+// choices made so far as JSON {shape: {"ctas_per_sm": k, "ms": [t1, t2, ...]}}
+void tc_autotune_enable(bool on);
+std::string tc_autotune_report();
 // throws DDTM_ERR_TIMEOUT if a tensor-core pass gave up waiting (and clears the flag)
 void check_tc_error(CoarseLevel& c);
 

@@ -25,6 +25,8 @@ void cuda_check(cudaError_t e, const char* what);
 // after every kernel launch: counts the launch (kernel_launches()) and checks it
 void cuda_check_launch(const char* what);
 long kernel_launches();
+// kernels launched by a graph replay count like direct launches
+void add_kernel_launches(long n);
 #define CK(x) ::ddtm::cuda_check((x), #x)
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
 // current device.  The attribute belongs to a (kernel, device) pair, so the
@@ -32,6 +34,16 @@ long kernel_launches();
 // threads.
 void set_dynamic_smem(const void* kernel, size_t bytes);
 #define CKL(what) ::ddtm::cuda_check_launch(what)
+
+// Device bytes held by the library's allocations (every DevBuf of the
+// process) and the optional cap on them (0: none); an allocation beyond the
+// cap throws DDTM_ERR_OOM without calling cudaMalloc.
+size_t device_bytes_in_use();
+void set_device_memory_limit(size_t bytes);
+size_t device_memory_limit();
+// changes whenever any library device buffer is allocated or freed (a cached
+// CUDA graph is valid only within one generation: its kernels hold pointers)
+long alloc_generation();
 
 // Owned device allocation.
 struct DevBuf {
@@ -154,6 +166,13 @@ struct ddtm_ctx {
   // pinned host scratch and named event pairs (created on first use, kept)
   std::map<std::string, std::pair<void*, size_t>> host_bufs;
   std::map<std::string, std::pair<cudaEvent_t, cudaEvent_t>> event_pairs;
+  // CUDA graphs of repeated launch sequences (one coarsest-GMRES iteration),
+  // keyed by everything their kernels' arguments depend on; value: the
+  // executable graph and its number of kernel nodes
+  std::map<std::string, std::pair<cudaGraphExec_t, int>> graphs;
+  bool use_graphs = true;   // option "graphs"
+  long graphs_gen = -1;     // allocation generation the cached graphs belong to
+  cudaStream_t capture_stream = nullptr;  // private stream that graphs are captured on
   void* scratch_host(const std::string& name, size_t bytes);
   void events(const std::string& name, cudaEvent_t ev[2]);
   ~ddtm_ctx();

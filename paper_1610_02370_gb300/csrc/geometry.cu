@@ -20,6 +20,7 @@ namespace ddtm {
 
 static std::atomic<long> g_kernel_launches{0};
 long kernel_launches() { return g_kernel_launches.load(); }
+void add_kernel_launches(long n) { g_kernel_launches.fetch_add(n); }
 void cuda_check_launch(const char* what) {
   g_kernel_launches.fetch_add(1);
   cuda_check(cudaGetLastError(), what);
@@ -44,8 +45,22 @@ void set_dynamic_smem(const void* kernel, size_t bytes) {
   have = bytes;
 }
 
+// Device bytes held by every DevBuf of the process, and the caller's budget
+// for them (0: none).
+static std::atomic<size_t> g_dev_bytes{0};
+static std::atomic<long> g_alloc_gen{0};  // bumped by every device allocation and free of a DevBuf
+long alloc_generation() { return g_alloc_gen.load(); }
+static std::atomic<size_t> g_dev_limit{0};
+size_t device_bytes_in_use() { return g_dev_bytes.load(); }
+void set_device_memory_limit(size_t bytes) { g_dev_limit.store(bytes); }
+size_t device_memory_limit() { return g_dev_limit.load(); }
+
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    cudaFree(p);
+    g_dev_bytes.fetch_sub(bytes);
+    g_alloc_gen.fetch_add(1);
+  }
   p = nullptr;
   bytes = 0;
 }
@@ -54,6 +69,11 @@ void DevBuf::ensure(size_t n) {
   if (n <= bytes && p) return;
   release();
   if (n == 0) return;
+  const size_t lim = g_dev_limit.load();
+  if (lim && g_dev_bytes.load() + n > lim)
+    throw Error(DDTM_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes would exceed the library's "
+                                  "memory limit of " + std::to_string(lim) + " bytes (" +
+                                  std::to_string(g_dev_bytes.load()) + " in use)");
   cudaError_t e = cudaMalloc(&p, n);
   if (e != cudaSuccess) {
     p = nullptr;
@@ -61,6 +81,8 @@ void DevBuf::ensure(size_t n) {
     throw Error(DDTM_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed");
   }
   bytes = n;
+  g_dev_bytes.fetch_add(n);
+  g_alloc_gen.fetch_add(1);
 }
 
 ScratchPool::~ScratchPool() {

@@ -55,7 +55,7 @@ __device__ __forceinline__ void cta_sum3(R& a, R& b, R& c, R* red) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, P == PREC_F64 ? 2 : 3) k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, SiteInv<P> Ainv, Geo g,
+__global__ void __launch_bounds__(128, P == PREC_F64 ? 2 : 4) k_sap_half(Spinor<P> x, Spinor<P> b, Links<P> U, Clover<P> C, SiteInv<P> Ainv, Geo g,
                            SapArgs<typename Prec<P>::real> a) {
   typedef typename Prec<P>::real R;
   typedef cplx<R> Z;

@@ -16,6 +16,7 @@
 #include "coarse.h"
 #include "common.cuh"
 #include "ddtm_internal.h"
+#include "timer.h"
 #include "solver.h"
 
 using namespace ddtm;
@@ -144,6 +145,69 @@ static const void* P_for(ddtm_ctx* c, int prec, int* pprec) {
 // The input is a batch of vectors of type tag in_type (1 FP32, 2 FP16; see blas.h).
 typedef std::function<void(cplx<float>*, const void*, int)> OpF32;
 
+// Runs body() (kernel launches on c->stream and on the Blas stream *bst) as a
+// CUDA graph keyed by key: the first time a key is met in an allocation
+// generation the launches run directly (they may allocate); the second time
+// they are captured on the context's private capture stream, instantiated and
+// replayed; afterwards every call is one graph launch on c->stream.  The key
+// must name everything the launches' arguments depend on besides device
+// buffers (their addresses are fixed within a generation).
+static void run_as_graph(ddtm_ctx* c, const std::string& key, cudaStream_t* bst, const std::function<void()>& body) {
+  if (!c->use_graphs || timer_on()) {
+    body();
+    return;
+  }
+  const long gen = alloc_generation();
+  if (gen != c->graphs_gen) {  // buffers moved: every cached graph is stale
+    for (auto& kv : c->graphs)
+      if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+    c->graphs.clear();
+    c->graphs_gen = gen;
+  }
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    body();
+    if (alloc_generation() == gen) c->graphs.emplace(key, std::make_pair((cudaGraphExec_t) nullptr, 0));
+    return;
+  }
+  if (it->second.first) {
+    CK(cudaGraphLaunch(it->second.first, c->stream));
+    add_kernel_launches(it->second.second);
+    return;
+  }
+  if (!c->capture_stream) CK(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+  // the capture stream starts after everything issued so far on c->stream
+  cudaEvent_t ev[2];
+  c->events("graph_capture", ev);
+  CK(cudaEventRecord(ev[0], c->stream));
+  CK(cudaStreamWaitEvent(c->capture_stream, ev[0], 0));
+  const cudaStream_t saved = c->stream, saved_b = *bst;
+  cudaGraph_t graph = nullptr;
+  const long before = kernel_launches();
+  c->stream = *bst = c->capture_stream;
+  CK(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    body();
+  } catch (...) {
+    cudaStreamEndCapture(c->capture_stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    c->stream = saved;
+    *bst = saved_b;
+    throw;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(c->capture_stream, &graph);
+  c->stream = saved;
+  *bst = saved_b;
+  CK(ec);
+  const long nk = kernel_launches() - before;  // counted once now, for the replay below
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(ei);
+  it->second = std::make_pair(exec, (int)nk);
+  CK(cudaGraphLaunch(exec, c->stream));
+}
+
 // Lockstep GMRES(m) with restarts for R systems A x_r = b_r (complex FP32
 // vectors of L entries each, interleaved; FP64 inner products).  Every
 // iteration orthogonalises all R Krylov vectors with one multi-dot and one
@@ -160,7 +224,7 @@ typedef std::function<void(cplx<float>*, const void*, int)> OpF32;
 // product with it is formed in FP32, so the Arnoldi relation holds to FP16
 // rounding of the basis, far below the loose tolerances of the coarsest solve.
 static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float>* b, size_t L, int R, int m, int max_restarts,
-                   double tol, double* relres, const char* tag, bool half_basis) {
+                   double tol, double* relres, const char* tag, bool half_basis, const std::string& op_key) {
   Blas B(c->stream, &c->scratch, &c->ring);
   std::string t(tag);
   const size_t N = L * R;
@@ -232,16 +296,28 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
     B.scale_dev(ad.scale, vs(w), vsb(Vj(0)));
     int k = 0;
     for (int j = 0; j < m; j++) {
-      A(w, Vj(j), vt);
-      B.dots_dev(vsb(V), N, j + 1, vs(w), h);
-      B.maxpy_dev(vs(w), vsb(V), N, j + 1, h, -1.0, reorth ? nullptr : nr2);
-      if (reorth) {
-        B.dots_dev(vsb(V), N, j + 1, vs(w), h2);
-        B.maxpy_dev(vs(w), vsb(V), N, j + 1, h2, -1.0, nr2);
+      auto iteration = [&]() {
+        A(w, Vj(j), vt);
+        B.dots_dev(vsb(V), N, j + 1, vs(w), h);
+        B.maxpy_dev(vs(w), vsb(V), N, j + 1, h, -1.0, reorth ? nullptr : nr2);
+        if (reorth) {
+          B.dots_dev(vsb(V), N, j + 1, vs(w), h2);
+          B.maxpy_dev(vs(w), vsb(V), N, j + 1, h2, -1.0, nr2);
+        }
+        launch_arnoldi_step(ad, j, h, reorth ? h2 : nullptr, nr2, c->stream, tol >= 1e-3);
+        CK(cudaMemcpyAsync(est_h + (size_t)(j & 1) * R, ad.est, R * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+        if (j < m - 1) B.scale_dev(ad.scale, vs(w), vsb(Vj(j + 1)));  // V_{j+1} = w / ||w||
+      };
+      if (op_key.empty()) {
+        iteration();
+      } else {
+        char kb[160];
+        snprintf(kb, sizeof(kb), "%s|j%d|R%d|m%d|L%zu|%d%d|est%p|", t.c_str(), j, R, m, L, (int)reorth,
+                 (int)half_basis, (void*)est_h);
+        run_as_graph(c, std::string(kb) + op_key, &B.st, iteration);
       }
-      launch_arnoldi_step(ad, j, h, reorth ? h2 : nullptr, nr2, c->stream, tol >= 1e-3);
-      fetch_est(j & 1);
-      if (j < m - 1) B.scale_dev(ad.scale, vs(w), vsb(Vj(j + 1)));  // V_{j+1} = w / ||w||
+      CK(cudaEventRecord(ev[j & 1], c->stream));
       iters++;
       k = j + 1;
       if (j >= 1) {  // estimates of the previous iteration
@@ -347,7 +423,10 @@ int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full,
     };
   }
   // FP16 Krylov basis with the tensor-core stencil (which reads FP16 operands anyway)
-  int it = gmres_b(c, Dhat, xo, bo, no * n, Rc, restart, max_restarts, tol, relres, "cgm", L.prec == PREC_F16);
+  char ok[96];  // what the operator's launch arguments depend on besides buffers
+  snprintf(ok, sizeof(ok), "eo|mu%.17g|p%d|lev%p", mu_c, L.prec, (const void*)&L);
+  int it = gmres_b(c, Dhat, xo, bo, no * n, Rc, restart, max_restarts, tol, relres, "cgm", L.prec == PREC_F16,
+                   std::string(ok));
   launch_coarse_even(L, te, be, xo, Rc, 1.f, -1.f, c->stream);  // phi_e = D_ee^-1 (eta_e - D_eo phi_o)
   launch_parity_copy(L, 0, te, x_full, Rc, 1, c->stream);
   launch_parity_copy(L, 1, xo, x_full, Rc, 1, c->stream);
@@ -886,7 +965,13 @@ static int solve_batch(ddtm_ctx* ctx, int nrhs) {
                      (size_t)g.V * (m + 2) * sizeof(float);
   const size_t held = ctx->scratch.held("out_") + ctx->scratch.held("solve_");
   const size_t reserve = tot / 10;
-  const size_t avail = fr + held > reserve ? fr + held - reserve : 0;
+  size_t avail = fr + held > reserve ? fr + held - reserve : 0;
+  const size_t cap = device_memory_limit();  // the caller's budget, if any, bounds the batch as well
+  if (cap) {
+    const size_t in_use = device_bytes_in_use();
+    const size_t room = cap > in_use ? cap - in_use + held : held;
+    if (room < avail) avail = room;
+  }
   int R = per > 0 ? (int)(avail / per) : nrhs;
   if (R < 1) R = 1;
   if (R > kMaxBatch) R = kMaxBatch;  // interleaved coarse batches hold at most kMaxBatch columns

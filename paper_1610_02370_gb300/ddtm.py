@@ -74,12 +74,18 @@ SIGNATURES = {
     "ddtm_apply_Dc": (_I, [_P, _I, _P, _P, _I, _D, _I]),
     "ddtm_coarse_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I)]),
     "ddtm_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(ddtm_solve_info)]),
+    "ddtm_eo_cg": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, ctypes.POINTER(ddtm_solve_info)]),
     "ddtm_save_setup": (_I, [_P, ctypes.c_char_p]),
     "ddtm_load_setup": (_I, [_P, ctypes.c_char_p]),
     "ddtm_timer_enable": (_I, [_P, _I]),
     "ddtm_timer_reset": (_I, [_P]),
     "ddtm_timer_report": (_I, [_P, ctypes.c_char_p, _I]),
     "ddtm_measure_fma_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "ddtm_set_memory_limit": (_I, [ctypes.c_size_t]),
+    "ddtm_set_option": (_I, [_P, ctypes.c_char_p, _I]),
+    "ddtm_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_I)]),
+    "ddtm_autotune_report": (_I, [ctypes.c_char_p, _I]),
+    "ddtm_memory_in_use": (_I, [ctypes.POINTER(ctypes.c_size_t)]),
 }
 for _name, (_res, _args) in SIGNATURES.items():
     _f = getattr(_lib, _name)
@@ -266,6 +272,16 @@ def ddtm_solve(ctx, x, b, nrhs, mu):
     return info, code
 
 
+def ddtm_eo_cg(ctx, x, b, nrhs, mu, tol=1e-10, max_iter=100000):
+    """Even-odd CG baseline (FP64); returns (info, code) like ddtm_solve."""
+    bxx, bb = _buf(x, True), _buf(b)
+    info = ddtm_solve_info()
+    code = _lib.ddtm_eo_cg(ctx, bxx[0], bb[0], nrhs, mu, tol, max_iter, _same_loc(bxx, bb), ctypes.byref(info))
+    if code not in (OK, ERR_NOCONV):
+        _check(ctx, code)
+    return info, code
+
+
 def ddtm_save_setup(ctx, path):
     _check(ctx, _lib.ddtm_save_setup(ctx, path.encode()))
 
@@ -306,3 +322,32 @@ def ddtm_measure_fma_peak(prec):
     f, ms, sms = _D(0), _D(0), _I(0)
     _check(None, _lib.ddtm_measure_fma_peak(prec, ctypes.byref(f), ctypes.byref(ms), ctypes.byref(sms)))
     return f.value, ms.value, sms.value
+
+
+def ddtm_set_memory_limit(nbytes):
+    """Cap the library's device memory (bytes, all contexts); 0 removes the cap."""
+    _check(None, _lib.ddtm_set_memory_limit(int(nbytes)))
+
+
+def ddtm_memory_in_use():
+    n = ctypes.c_size_t(0)
+    _check(None, _lib.ddtm_memory_in_use(ctypes.byref(n)))
+    return n.value
+
+
+def ddtm_set_option(ctx, name, value):
+    _check(ctx, _lib.ddtm_set_option(ctx, name.encode(), int(value)))
+
+
+def ddtm_get_option(ctx, name):
+    v = _I(0)
+    _check(ctx, _lib.ddtm_get_option(ctx, name.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def ddtm_autotune_report():
+    """{shape: {"ctas_per_sm": k, "ms": [...]}} chosen by the tensor-core pass autotuner so far."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(None, _lib.ddtm_autotune_report(buf, len(buf)))
+    return json.loads(buf.value.decode())

@@ -283,3 +283,46 @@ def test_solve_fp32_coarse_many_rhs(lib):
             assert rel <= 1e-10, (r, rel)
     finally:
         lib.ddtm_destroy(ctx)
+
+
+def test_error_statuses_noconv_and_oom(lib):
+    """DDTM_ERR_NOCONV: an outer iteration budget too small for 1e-10 stops the solve, which still fills
+    the report with the achieved residual.  DDTM_ERR_OOM: a device-memory cap below what the setup
+    needs fails that call (no cudaMalloc is attempted past the cap) and leaves the context usable."""
+    dims, block = (8, 8, 8, 8), (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=0)
+    ctx = make_ctx(lib, dims, block, U, 0.13, 1.2, 8, n_setup=2, post_smooth=2)
+    try:
+        lib.ddtm_setup(ctx, 0.01, 5)
+        p = lib.ddtm_get_params(ctx)
+        p.outer_max_iters = 2
+        lib.ddtm_set_params(ctx, p)
+        b = synth.gaussian_spinor(dims, seed=1).cuda()
+        x = torch.zeros_like(b)
+        info, code = lib.ddtm_solve(ctx, x, b, 1, 0.01)
+        assert code == lib.ERR_NOCONV
+        assert 0 < info.iters <= 2 and 1e-10 < info.max_relres < 1.0
+        p.outer_max_iters = 1000
+        lib.ddtm_set_params(ctx, p)
+        info, code = lib.ddtm_solve(ctx, x, b, 1, 0.01)
+        assert code == lib.OK
+        used = lib.ddtm_memory_in_use()
+        assert used > 0
+        lib.ddtm_set_memory_limit(used + 4096)
+        try:
+            with pytest.raises(lib.DDTMError) as e:
+                lib.ddtm_field_create(ctx, lib.PREC_F32, 1)  # one fine field: 8^4 x 12 x 8 bytes > 4 KB
+            assert e.value.code == lib.ERR_OOM and "memory limit" in str(e.value)
+            assert lib.ddtm_memory_in_use() == used
+            # a 3-rhs solve under the cap goes in batches that fit in what the context already holds
+            b3 = synth.gaussian_spinor(dims, seed=2, nrhs=3).cuda()
+            x3 = torch.zeros_like(b3)
+            info, code = lib.ddtm_solve(ctx, x3, b3, 3, 0.01)
+            assert code == lib.OK and info.max_relres <= 1e-10
+            assert lib.ddtm_memory_in_use() <= used + 4096
+        finally:
+            lib.ddtm_set_memory_limit(0)
+        f = lib.ddtm_field_create(ctx, lib.PREC_F32, 1)
+        lib.ddtm_field_destroy(f)
+    finally:
+        lib.ddtm_destroy(ctx)
