@@ -138,6 +138,15 @@ int ddtm_set_params(ddtm_ctx* ctx, const ddtm_params* p);
  * NaN/Inf. */
 int ddtm_load_gauge(ddtm_ctx* ctx, const double* U, int loc, double kappa, double c_sw);
 
+/* Twisted boundary conditions psi(x + L_mu mu_hat) = exp(i theta_mu) psi(x)
+ * for mu = t, x, y, z (a library feature the paper lists for its HMC use,
+ * Sec. 3.2 and the appendix): applied to the links U_mu(x) at x_mu = L_mu - 1
+ * (the clover term, built from closed loops, is unchanged), on top of the
+ * antiperiodic t of ddtm_create.  May be called before or after
+ * ddtm_load_gauge; a change invalidates the setup.  theta = {0, 0, 0, 0}
+ * restores periodic boundaries. */
+int ddtm_set_boundary_phases(ddtm_ctx* ctx, const double theta[4]);
+
 /* y = D(mu) x for nrhs right-hand sides (canonical spinors), computed in
  * storage precision prec (Sec. 2.1; mu may be +mu or -mu, the two flavours). */
 int ddtm_apply_D(ddtm_ctx* ctx, double* y, const double* x, int nrhs, double mu, int prec, int loc);
@@ -191,10 +200,21 @@ int ddtm_sap_field(ddtm_ctx* ctx, ddtm_field* x, const ddtm_field* b, double mu,
  * the current multigrid; P and the coarse operators are rebuilt after each. */
 int ddtm_setup(ddtm_ctx* ctx, double mu, uint64_t seed);
 
-/* Replace the test vectors of level 0 by v (nv canonical fine spinors),
- * orthonormalise them per aggregate half (Gamma5-compatible aggregation,
- * Sec. 2.3) into P, and build the coarse operator D_1 = P^+ D P.  Test hook
- * for parity against an independent implementation; nv must equal params.nv[0]. */
+/* Update an existing setup (the HMC usage of Sec. 3.2: after the gauge field
+ * (ddtm_load_gauge) or the twist changed): the test vectors of the last
+ * setup are kept, P and the coarse operators are rebuilt from them with the
+ * current gauge field, and n_iter inverse-iteration steps (Sec. 2.6, k >= 2)
+ * at twist mu follow (n_iter = 0: rebuild only).  DDTM_ERR_STATE if no
+ * test vectors of the current parameters exist. */
+int ddtm_setup_update(ddtm_ctx* ctx, double mu, int n_iter);
+
+/* Replace the test vectors of level `level` (0, or 1 of three levels) by v
+ * (nv canonical fine spinors for level 0, nv canonical level-1 coarse vectors
+ * for level 1), orthonormalise them per aggregate half (Gamma5-compatible
+ * aggregation, Sec. 2.3) into P_level, and build the operator of the next
+ * level, D_{level+1} = P^+ D_level P.  Test hook for parity against an
+ * independent implementation; nv must equal params.nv[level]; level 1 needs
+ * the level-0 vectors first. */
 int ddtm_set_test_vectors(ddtm_ctx* ctx, int level, const double* v, int nv, int loc);
 
 /* Rebuild every coarse operator from the current P (Galerkin, Sec. 2.3). */
@@ -215,6 +235,16 @@ int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* c, int nrhs,
  * operand images on the tensor cores with FP32 accumulation (coarse_prec
  * F16; DDTM_ERR_TIMEOUT if a pipeline wait of that kernel gave up). */
 int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs, double mu, int loc);
+
+/* x = ncycles red-black SAP cycles on D_level(mu) x = b from x = 0 on a
+ * coarse level (Sec. 2.4 applied to the Galerkin operator, the smoother of
+ * the intermediate level of three, Sec. 2.2): the blocks are the level's
+ * aggregates (block[level]), each block system (hops leaving the block
+ * dropped) gets nmr minimal-residual steps on the full block from zero, red
+ * blocks first.  Vectors in the canonical coarse layout of that level.  Test
+ * hook; level must be 1 with n_levels = 3 (DDTM_ERR_ARG otherwise). */
+int ddtm_sap_coarse(ddtm_ctx* ctx, int level, double* x, const double* b, int nrhs, double mu, int ncycles, int nmr,
+                    int loc);
 
 /* Even-odd preconditioned GMRES on the coarsest level (Sec. 2.5) for
  * D_c(mu_c) x = b with mu_c as given; restart length, restarts and tolerance

@@ -233,8 +233,13 @@ int ddtm_set_params(ddtm_ctx* ctx, const ddtm_params* p) {
   validate_params(ctx, *p);
   bool hierarchy_changed = p->n_levels != ctx->p.n_levels || p->nv[0] != ctx->p.nv[0] || p->nv[1] != ctx->p.nv[1] ||
                            memcmp(p->block, ctx->p.block, sizeof(p->block)) != 0 || p->coarse_prec != ctx->p.coarse_prec;
+  const bool block1_changed = memcmp(p->block[1], ctx->p.block[1], sizeof(p->block[1])) != 0;
   ctx->p = *p;
   if (hierarchy_changed) invalidate_setup(ctx);
+  if (block1_changed) {  // the level-1 aggregates and the level-2 lattice follow block[1]
+    ctx->a1.geom = false;
+    ctx->c2_geom = false;
+  }
   API_END(ctx)
 }
 
@@ -264,9 +269,31 @@ int ddtm_load_gauge(ddtm_ctx* ctx, const double* U, int loc, double kappa, doubl
   ctx->csw = c_sw;
   double m = 1.0 / (2.0 * kappa) - 4.0;
   launch_clover_build(ctx->g, ctx->clover[0].as<double>(), dU, m + 4.0, c_sw, ctx->stream);
+  if (ctx->theta[0] != 0 || ctx->theta[1] != 0 || ctx->theta[2] != 0 || ctx->theta[3] != 0)
+    launch_link_phases(ctx->g, ctx->links[0].as<double>(), ctx->theta, ctx->stream);  // after the clover term
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->gauge = true;
   invalidate_setup(ctx);
+  API_END(ctx)
+}
+
+int ddtm_set_boundary_phases(ddtm_ctx* ctx, const double theta[4]) {
+  API_BEGIN(ctx)
+  if (!theta) throw Error(DDTM_ERR_ARG, "null theta");
+  for (int m = 0; m < 4; m++)
+    if (!std::isfinite(theta[m])) throw Error(DDTM_ERR_ARG, "non-finite boundary phase");
+  if (ctx->gauge) {
+    // change the phases of the loaded links by the difference, drop the lower-precision copies
+    // (converted again on first use) and the setup (the operator changed)
+    double d[4];
+    for (int m = 0; m < 4; m++) d[m] = theta[m] - ctx->theta[m];
+    launch_link_phases(ctx->g, ctx->links[0].as<double>(), d, ctx->stream);
+    ctx->links[1].release();
+    ctx->links[2].release();
+    CK(cudaStreamSynchronize(ctx->stream));
+    invalidate_setup(ctx);
+  }
+  for (int m = 0; m < 4; m++) ctx->theta[m] = theta[m];
   API_END(ctx)
 }
 

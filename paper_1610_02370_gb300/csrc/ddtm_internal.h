@@ -93,6 +93,24 @@ struct CoarseLevel {
   bool built = false;
 };
 
+// Aggregation of the level-1 lattice (three-level hierarchies, Sec. 2.3 applied
+// to D_1): aggregates are blocks of b[4] level-1 sites (also the blocks of the
+// level-1 SAP smoother, Sec. 2.4); they are the sites of level 2, in canonical
+// order over the NB[4] block lattice.  Within an aggregate the sites are
+// numbered q in canonical order of their offsets.
+struct Level1Agg {
+  int b[4] = {0, 0, 0, 0}, NB[4] = {0, 0, 0, 0};
+  int Nagg = 0, Vb = 0;
+  int nv = 0;                 // level-1 test vectors (columns of P_1 per aggregate half)
+  std::vector<int> h_sites;   // [Nagg][Vb] level-1 site of local index q
+  DevBuf sites;               // device copy of h_sites
+  DevBuf colour;              // [2][Nagg/2]: aggregates of colour 0 (red), then colour 1
+  DevBuf tabs;                // [9][8][Nc1 + 1] neighbour tables of the Galerkin parts (see level1.cu)
+  DevBuf tv;                  // [nv][Nc1][n1] level-1 test vectors, complex FP32
+  DevBuf P;                   // [Nagg][2][nv][Vb][n1/2] P_1, complex FP32
+  bool geom = false;
+};
+
 // faces of a block: for hop k, the sites whose hop leaves the block
 struct FaceDev {
   DevBuf idx, list;
@@ -142,6 +160,7 @@ struct ddtm_ctx {
   ddtm_params p;
   bool gauge = false;
   double kappa = 0, csw = 0;
+  double theta[4] = {0, 0, 0, 0};  // twisted boundary phases applied to the internal links
   ddtm::DevBuf links[3];   // per precision, internal layout
   ddtm::DevBuf clover[3];  // per precision, packed site term (incl. m+4)
   ddtm::DevBuf sinv[3];    // per precision, even-site inverse of site term + i mu gamma5
@@ -156,6 +175,10 @@ struct ddtm_ctx {
   bool faces_ready = false;
   ddtm::CoarseLevel c1;
   bool c1_geom = false;
+  // three levels: aggregation of level 1 and the coarsest operator D_2
+  ddtm::Level1Agg a1;
+  ddtm::CoarseLevel c2;
+  bool c2_geom = false;
   long coarse_iters = 0;   // accumulated by the coarsest solves
   ddtm::CoefRing ring;     // coefficient transfers of the Krylov solvers
   bool have_P = false;
@@ -183,6 +206,10 @@ namespace ddtm {
 // ---- geometry.cu -------------------------------------------------------------
 void build_geometry(FineGeom& g);
 void build_coarse_geometry(const FineGeom& g, CoarseLevel& c);
+// neighbour tables and parity lists of a coarse lattice with extents lat[4] (mu order)
+void build_coarse_geometry_lat(const int lat[4], CoarseLevel& c);
+// aggregates of b[4] sites on the level-1 lattice of c1
+void build_level1_aggregates(const CoarseLevel& c1, const int b[4], Level1Agg& a);
 // canonical FP64 complex spinor (one rhs) <-> internal field of precision prec
 void launch_spinor_from_canon(const FineGeom& g, int prec, void* d, float* nrm, const double* in, cudaStream_t s);
 void launch_spinor_to_canon(const FineGeom& g, int prec, const void* d, const float* nrm, double* out, cudaStream_t s);
@@ -190,6 +217,8 @@ void launch_spinor_to_canon(const FineGeom& g, int prec, const void* d, const fl
 void launch_links_from_canon(const FineGeom& g, double* out, const double* U, cudaStream_t s);
 // element-wise precision conversion of complex arrays (double2 -> float2 / half2)
 void launch_convert_complex(const double* in, int prec_out, void* out, size_t n, cudaStream_t s);
+// U_mu(x) *= exp(i phase[mu]) on the sites with x_mu = L_mu - 1 (internal FP64 links)
+void launch_link_phases(const FineGeom& g, double* links, const double phase[4], cudaStream_t s);
 // count non-finite doubles
 void launch_count_nonfinite(const double* a, size_t n, int* counter, cudaStream_t s);
 

@@ -200,9 +200,64 @@ void build_geometry(FineGeom& g) {
   CK(cudaMemcpy(g.blk_nbr.p, g.h_blk_nbr.data(), g.h_blk_nbr.size() * 4, cudaMemcpyHostToDevice));
 }
 
-void build_coarse_geometry(const FineGeom& g, CoarseLevel& c) {
-  for (int m = 0; m < 4; m++) c.lat[m] = g.NB[m];
-  c.Nc = g.Nb;
+void build_coarse_geometry(const FineGeom& g, CoarseLevel& c) { build_coarse_geometry_lat(g.NB, c); }
+
+void build_level1_aggregates(const CoarseLevel& c1, const int b[4], Level1Agg& a) {
+  a.Vb = 1;
+  a.Nagg = 1;
+  for (int m = 0; m < 4; m++) {
+    if (b[m] < 1 || c1.lat[m] % b[m]) throw Error(DDTM_ERR_ARG, "level-1 block extents must divide the level-1 lattice");
+    a.b[m] = b[m];
+    a.NB[m] = c1.lat[m] / b[m];
+    if (a.NB[m] % 2) throw Error(DDTM_ERR_ARG, "level-1 blocks per direction must be even (red-black SAP)");
+    a.Vb *= b[m];
+    a.Nagg *= a.NB[m];
+  }
+  a.h_sites.assign((size_t)a.Nagg * a.Vb, 0);
+  std::vector<int> col[2];
+  for (int A = 0; A < a.Nagg; A++) {
+    int B[4];
+    canon_coords(a.NB, A, B);
+    col[(B[0] + B[1] + B[2] + B[3]) & 1].push_back(A);
+    for (int q = 0; q < a.Vb; q++) {
+      int o[4], x[4];
+      canon_coords(a.b, q, o);
+      for (int m = 0; m < 4; m++) x[m] = B[m] * a.b[m] + o[m];
+      a.h_sites[(size_t)A * a.Vb + q] = canon_index(c1.lat, x);
+    }
+  }
+  a.sites.ensure(a.h_sites.size() * 4);
+  CK(cudaMemcpy(a.sites.p, a.h_sites.data(), a.h_sites.size() * 4, cudaMemcpyHostToDevice));
+  std::vector<int> cl(col[0]);
+  cl.insert(cl.end(), col[1].begin(), col[1].end());
+  a.colour.ensure(cl.size() * 4);
+  CK(cudaMemcpy(a.colour.p, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice));
+  // Galerkin parts (level1.cu): table t = 0 keeps the hops that stay inside the aggregate, table
+  // t = 1 + k only hop k where it leaves the aggregate; every other hop reads the zero site Nc1
+  const int Nc = c1.Nc;
+  std::vector<int> agg_of(Nc);
+  for (int A = 0; A < a.Nagg; A++)
+    for (int q = 0; q < a.Vb; q++) agg_of[a.h_sites[(size_t)A * a.Vb + q]] = A;
+  std::vector<int> tabs((size_t)9 * 8 * Nc);
+  for (int t = 0; t < 9; t++)
+    for (int k = 0; k < 8; k++)
+      for (int i = 0; i < Nc; i++) {
+        const int nb = c1.h_nbr[(size_t)k * Nc + i];
+        const bool cross = agg_of[nb] != agg_of[i];  // NB >= 2 in every direction
+        const bool keep = t == 0 ? !cross : (k == t - 1 && cross);
+        tabs[((size_t)t * 8 + k) * Nc + i] = keep ? nb : Nc;
+      }
+  a.tabs.ensure(tabs.size() * 4);
+  CK(cudaMemcpy(a.tabs.p, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice));
+  a.geom = true;
+}
+
+void build_coarse_geometry_lat(const int lat[4], CoarseLevel& c) {
+  c.Nc = 1;
+  for (int m = 0; m < 4; m++) {
+    c.lat[m] = lat[m];
+    c.Nc *= lat[m];
+  }
   c.h_nbr.assign(8 * c.Nc, 0);
   c.h_even.clear();
   c.h_odd.clear();
@@ -237,6 +292,52 @@ void build_coarse_geometry(const FineGeom& g, CoarseLevel& c) {
   CK(cudaMemcpy(c.nbr.p, c.h_nbr.data(), c.h_nbr.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c.even.p, c.h_even.data(), c.h_even.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c.odd.p, c.h_odd.data(), c.h_odd.size() * 4, cudaMemcpyHostToDevice));
+}
+
+// ---- twisted boundary conditions as boundary-link phases --------------------------
+// A hop that wraps forward in direction mu reads exp(i theta_mu) psi, one that wraps backward
+// exp(-i theta_mu) psi; both are the hops of the links U_mu(x) at x_mu = L_mu - 1, so multiplying those
+// links by exp(i theta_mu) gives the twisted operator (closed loops, hence the clover term, unchanged).
+struct PhaseMap {
+  int L[4], b[4], NB[4], Vb, Nb;
+  double c[4], s[4];
+  const uint32_t* loc_coord;
+};
+__global__ void k_link_phases(double2* __restrict__ U, PhaseMap m) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)m.Vb * m.Nb) return;
+  const int blk = (int)(t / m.Vb), loc = (int)(t - (long)blk * m.Vb);
+  int B[4], r = blk;
+  B[1] = r % m.NB[1]; r /= m.NB[1];
+  B[2] = r % m.NB[2]; r /= m.NB[2];
+  B[3] = r % m.NB[3];
+  B[0] = r / m.NB[3];
+  const uint32_t lc = m.loc_coord[loc];
+  for (int mu = 0; mu < 4; mu++) {
+    const int x = B[mu] * m.b[mu] + (int)((lc >> (8 * mu)) & 255);
+    if (x != m.L[mu] - 1 || (m.c[mu] == 1.0 && m.s[mu] == 0.0)) continue;
+    double2* u = U + ((size_t)(blk * 4 + mu) * 9) * m.Vb + loc;
+    for (int k = 0; k < 9; k++) {
+      const double2 a = u[(size_t)k * m.Vb];
+      u[(size_t)k * m.Vb] = make_double2(m.c[mu] * a.x - m.s[mu] * a.y, m.c[mu] * a.y + m.s[mu] * a.x);
+    }
+  }
+}
+
+void launch_link_phases(const FineGeom& g, double* links, const double phase[4], cudaStream_t s) {
+  PhaseMap m;
+  for (int i = 0; i < 4; i++) {
+    m.L[i] = g.L[i];
+    m.b[i] = g.b[i];
+    m.NB[i] = g.NB[i];
+    m.c[i] = cos(phase[i]);
+    m.s[i] = sin(phase[i]);
+  }
+  m.Vb = g.Vb;
+  m.Nb = g.Nb;
+  m.loc_coord = g.loc_coord.as<uint32_t>();
+  k_link_phases<<<(unsigned)((g.V + 127) / 128), 128, 0, s>>>((double2*)links, m);
+  CKL("link_phases");
 }
 
 // ---- canonical <-> internal ------------------------------------------------------

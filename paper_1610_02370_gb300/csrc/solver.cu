@@ -14,6 +14,7 @@
 
 #include "blas.h"
 #include "coarse.h"
+#include "level1.h"
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "timer.h"
@@ -25,7 +26,16 @@ typedef std::complex<double> zc;
 namespace ddtm {
 
 void validate_params(ddtm_ctx* c, const ddtm_params& p) {
-  if (p.n_levels != 2) throw Error(DDTM_ERR_ARG, "n_levels must be 2");
+  if (p.n_levels != 2 && p.n_levels != 3) throw Error(DDTM_ERR_ARG, "n_levels must be 2 or 3");
+  if (p.n_levels == 3) {
+    if (p.nv[1] < 1 || p.nv[1] > 32) throw Error(DDTM_ERR_ARG, "nv[1] must be in 1..32");
+    for (int m = 0; m < 4; m++)
+      if (p.block[1][m] < 1 || c->g.NB[m] % p.block[1][m] || (c->g.NB[m] / p.block[1][m]) % 2)
+        throw Error(DDTM_ERR_ARG, "block[1] must divide the level-1 lattice into an even number of blocks per "
+                                  "direction");
+    if (p.kcycle_restart < 1 || p.kcycle_restart > 64 || p.kcycle_max_restarts < 0 || !(p.kcycle_tol > 0))
+      throw Error(DDTM_ERR_ARG, "invalid K-cycle parameters");
+  }
   for (int m = 0; m < 4; m++)
     if (p.block[0][m] != c->g.b[m]) throw Error(DDTM_ERR_ARG, "block[0] is fixed at ddtm_create");
   if (p.nv[0] < 1 || p.nv[0] > 64) throw Error(DDTM_ERR_ARG, "nv[0] must be in 1..64");
@@ -48,7 +58,12 @@ void invalidate_setup(ddtm_ctx* c) {
   c->have_P = false;
   c->c1.built = false;
   c->c1.inv_valid = false;
+  c->c2.built = false;
+  c->c2.inv_valid = false;
 }
+
+// the level whose operator the even-odd GMRES of Sec. 2.5 inverts (with the shifted twist)
+static CoarseLevel& coarsest(ddtm_ctx* c) { return c->p.n_levels == 3 ? c->c2 : c->c1; }
 
 void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const float* bn, double mu, int ncycles, int nmr,
              bool from_zero, int R) {
@@ -115,7 +130,9 @@ void build_hierarchy(ddtm_ctx* c) {
   }
   L.nv = nv;
   L.n = 2 * nv;
-  L.prec = c->p.coarse_prec;
+  // with three levels, level 1 (the K-cycle's operator, SIMT) stays FP32; only the coarsest level
+  // runs on the tensor cores
+  L.prec = c->p.n_levels == 3 ? PREC_F32 : c->p.coarse_prec;
   L.Dc.ensure((size_t)L.Nc * 9 * L.n * L.n * 8);
   launch_galerkin(g, c->faces, PREC_F32, L.Dc.p, c->P0.as<float2>(), c->links[PREC_F32].p, c->clover[PREC_F32].p, nv,
                   L.prec == PREC_F16, c->stream);
@@ -125,9 +142,30 @@ void build_hierarchy(ddtm_ctx* c) {
   c->have_P = true;
 }
 
+// P_1 from the level-1 test vectors, then D_2 = P_1^+ D_1 P_1 (three levels)
+void build_hierarchy1(ddtm_ctx* c) {
+  CoarseLevel& L1 = c->c1;
+  Level1Agg& a = c->a1;
+  if (!a.geom) build_level1_aggregates(L1, c->p.block[1], a);
+  launch_l1_build_P(a, L1, c->stream);
+  CoarseLevel& L2 = c->c2;
+  if (!c->c2_geom) {
+    build_coarse_geometry_lat(a.NB, L2);
+    c->c2_geom = true;
+  }
+  L2.nv = a.nv;
+  L2.n = 2 * a.nv;
+  L2.prec = c->p.coarse_prec;
+  launch_l1_galerkin(a, L1, L2, c->scratch, c->stream);
+  if (L2.prec == PREC_F16) build_coarse_images(L2, c->stream);
+  L2.inv_valid = false;
+  L2.built = true;
+}
+
 void require_hierarchy(ddtm_ctx* c) {
   require_gauge(c);
-  if (!c->have_P || !c->c1.built) throw Error(DDTM_ERR_STATE, "no aggregation / coarse operator (call ddtm_setup)");
+  if (!c->have_P || !c->c1.built || (c->p.n_levels == 3 && !c->c2.built))
+    throw Error(DDTM_ERR_STATE, "no aggregation / coarse operator (call ddtm_setup)");
 }
 
 // P in the storage used by the transfer kernels of precision prec
@@ -223,15 +261,22 @@ static void run_as_graph(ddtm_ctx* c, const std::string& key, cudaStream_t* bst,
 // residual, the new vector before normalisation and x stay FP32); every
 // product with it is formed in FP32, so the Arnoldi relation holds to FP16
 // rounding of the basis, far below the loose tolerances of the coarsest solve.
+// With a preconditioner M (flexible GMRES, the K-cycle solver of intermediate
+// levels, Sec. 2.5): z_j = M v_j is kept (FP32) and w = A z_j; the update is
+// x += sum_j y_j z_j.
 static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float>* b, size_t L, int R, int m, int max_restarts,
-                   double tol, double* relres, const char* tag, bool half_basis, const std::string& op_key) {
+                   double tol, double* relres, const char* tag, bool half_basis, const std::string& op_key,
+                   const OpF32* M = nullptr) {
   Blas B(c->stream, &c->scratch, &c->ring);
   std::string t(tag);
   const size_t N = L * R;
+  if (M) half_basis = false;
   const int vt = half_basis ? 2 : 1;
   const size_t vb = half_basis ? sizeof(__half2) : sizeof(float2);
   char* V = (char*)c->scratch.get(t + (half_basis ? "_Vh" : "_V"), (size_t)(m + 1) * N * vb);
   auto Vj = [&](int j) { return (void*)(V + (size_t)j * N * vb); };
+  float2* Z = M ? (float2*)c->scratch.get(t + "_Z", (size_t)m * N * sizeof(float2)) : nullptr;
+  auto Zj = [&](int j) { return (cplx<float>*)(Z + (size_t)j * N); };
   cplx<float>* w = (cplx<float>*)c->scratch.get(t + "_w", N * sizeof(float2));
   // device bookkeeping, one block of scratch
   size_t nH = (size_t)R * (m + 1) * m, ncs = (size_t)R * m, ng = (size_t)R * (m + 1), nh = (size_t)(m + 1) * R;
@@ -297,7 +342,12 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
     int k = 0;
     for (int j = 0; j < m; j++) {
       auto iteration = [&]() {
-        A(w, Vj(j), vt);
+        if (M) {
+          (*M)(Zj(j), Vj(j), vt);
+          A(w, Zj(j), 1);
+        } else {
+          A(w, Vj(j), vt);
+        }
         B.dots_dev(vsb(V), N, j + 1, vs(w), h);
         B.maxpy_dev(vs(w), vsb(V), N, j + 1, h, -1.0, reorth ? nullptr : nr2);
         if (reorth) {
@@ -309,7 +359,7 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
                            c->stream));
         if (j < m - 1) B.scale_dev(ad.scale, vs(w), vsb(Vj(j + 1)));  // V_{j+1} = w / ||w||
       };
-      if (op_key.empty()) {
+      if (op_key.empty() || M) {
         iteration();
       } else {
         char kb[160];
@@ -339,7 +389,8 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
       done = all_done(est.data());
     }
     launch_arnoldi_solve(ad, k, y, c->stream);
-    B.maxpy_dev(vs(x), vsb(V), N, k, y, +1.0, nullptr);
+    if (M) B.maxpy_dev(vs(x), vs(Z), N, k, y, +1.0, nullptr);
+    else B.maxpy_dev(vs(x), vsb(V), N, k, y, +1.0, nullptr);
   }
   for (int r = 0; r < R; r++) relres[r] = est[r];
   return iters;
@@ -352,7 +403,7 @@ static int gmres_b(ddtm_ctx* c, const OpF32& A, cplx<float>* x, const cplx<float
 // receives the per-rhs estimates of the reduced system.
 int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full, int Rc, double mu_c, int restart,
                     int max_restarts, double tol, double* relres) {
-  CoarseLevel& L = c->c1;
+  CoarseLevel& L = coarsest(c);
   if (!L.inv_valid || L.inv_mu != mu_c) launch_self_inverse(L, mu_c, c->stream);
   size_t ne = L.h_even.size(), no = L.h_odd.size(), n = L.n;
   size_t bytes_e = ne * n * Rc * 8, bytes_o = no * n * Rc * 8;
@@ -434,12 +485,59 @@ int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full,
   return it;
 }
 
+// ---- level 1 of three (Sec. 2.2 K-cycle on the intermediate level) ------------------------
+// SAP on D_1(mu) for Rc interleaved level-1 vectors (Rc a multiple of 4): ncycles red-black
+// cycles, from x = 0 if from_zero, else from x
+static void sap_l1(ddtm_ctx* c, cplx<float>* x, const cplx<float>* b, double mu, int ncycles, int nmr, bool from_zero,
+                   int Rc) {
+  CoarseLevel& L1 = c->c1;
+  if (!c->a1.geom) build_level1_aggregates(L1, c->p.block[1], c->a1);  // the SAP blocks are the aggregates
+  if (from_zero) CK(cudaMemsetAsync(x, 0, (size_t)L1.Nc * L1.n * Rc * 8, c->stream));
+  for (int cyc = 0; cyc < ncycles; cyc++) {
+    launch_l1_sap_half(c->a1, L1, (float2*)x, (const float2*)b, 0, mu, nmr, Rc, c->stream);
+    launch_l1_sap_half(c->a1, L1, (float2*)x, (const float2*)b, 1, mu, nmr, Rc, c->stream);
+  }
+}
+
+// One application of the level-1 preconditioner: z = P_1 D_2(delta mu)^-1 R_1 v (even-odd GMRES on
+// the coarsest level), then post_smooth SAP cycles on D_1(mu) z = v started from that z.
+static void precondition_l1(ddtm_ctx* c, cplx<float>* z, const cplx<float>* v, double mu, int Rc) {
+  CoarseLevel& L2 = c->c2;
+  const size_t n2 = (size_t)L2.Nc * L2.n * Rc;
+  cplx<float>* c2 = (cplx<float>*)c->scratch.get("l1_c2", n2 * 8);
+  cplx<float>* e2 = (cplx<float>*)c->scratch.get("l1_e2", n2 * 8);
+  launch_l1_restrict(c->a1, c->c1, (float2*)c2, (const float2*)v, Rc, Rc, c->stream);
+  std::vector<double> rr(Rc);
+  coarse_eo_solve(c, e2, c2, Rc, c->p.delta * mu, c->p.coarse_restart, c->p.coarse_max_restarts, c->p.coarse_tol,
+                  rr.data());
+  launch_l1_prolong(c->a1, c->c1, (float2*)z, (const float2*)e2, Rc, Rc, 0, c->stream);
+  sap_l1(c, z, v, mu, c->p.post_smooth, c->p.nmr, false, Rc);
+}
+
+// x ~ D_1(mu)^-1 b: flexible GMRES(kcycle_restart) with kcycle_max_restarts restarts to
+// kcycle_tol, preconditioned by precondition_l1 (Table 1: FGMRES(5), 2 restarts, 1e-1)
+static void kcycle_l1(ddtm_ctx* c, cplx<float>* x, const cplx<float>* b, double mu, int Rc) {
+  CoarseLevel& L1 = c->c1;
+  OpF32 A = [&](cplx<float>* out, const void* in, int in_type) {
+    if (in_type != 1) throw Error(DDTM_ERR_ARG, "internal: level-1 operator takes FP32 vectors");
+    launch_coarse_apply_full(L1, out, (const cplx<float>*)in, Rc, mu, 3, 1.f, 0.f, c->stream);
+  };
+  OpF32 M = [&](cplx<float>* out, const void* in, int in_type) {
+    if (in_type != 1) throw Error(DDTM_ERR_ARG, "internal: level-1 preconditioner takes FP32 vectors");
+    precondition_l1(c, out, (const cplx<float>*)in, mu, Rc);
+  };
+  std::vector<double> rr(Rc);
+  gmres_b(c, A, x, b, (size_t)L1.Nc * L1.n, Rc, c->p.kcycle_restart, c->p.kcycle_max_restarts, c->p.kcycle_tol,
+          rr.data(), "kc1", false, std::string(), &M);
+}
+
 // ---- K-cycle preconditioner (Sec. 2.2): z = P D_c^-1 R v, then post-smoothing ----------
 // R fine fields of precision prec at stride 12 V (FP16 scales at stride V).
 void mg_precondition(ddtm_ctx* c, int prec, void* z, float* zn, const void* v, const float* vn, double mu, int R) {
   const FineGeom& g = c->g;
   CoarseLevel& L = c->c1;
-  const int Rc = coarse_batch(R);
+  // the level-1 SAP of three levels works on chunks of 4 right-hand sides
+  const int Rc = c->p.n_levels == 3 && coarse_batch(R) < 4 ? 4 : coarse_batch(R);
   size_t nc = (size_t)L.Nc * L.n * Rc;
   cplx<float>* cv = (cplx<float>*)c->scratch.get("mg_c", nc * 8);
   cplx<float>* ev = (cplx<float>*)c->scratch.get("mg_e", nc * 8);
@@ -447,9 +545,13 @@ void mg_precondition(ddtm_ctx* c, int prec, void* z, float* zn, const void* v, c
   int pprec;
   const void* P = P_for(c, prec, &pprec);
   launch_restrict(g, prec, cv, v, vn, P, pprec, L.nv, R, Rc, c->stream);
-  std::vector<double> rr(Rc);
-  coarse_eo_solve(c, ev, cv, Rc, c->p.delta * mu, c->p.coarse_restart, c->p.coarse_max_restarts, c->p.coarse_tol,
-                  rr.data());
+  if (c->p.n_levels == 3) {
+    kcycle_l1(c, ev, cv, mu, Rc);  // level 1 keeps the twist mu; the coarsest level uses delta mu
+  } else {
+    std::vector<double> rr(Rc);
+    coarse_eo_solve(c, ev, cv, Rc, c->p.delta * mu, c->p.coarse_restart, c->p.coarse_max_restarts, c->p.coarse_tol,
+                    rr.data());
+  }
   launch_prolong(g, prec, z, zn, ev, P, pprec, L.nv, R, Rc, 0, c->stream);
   sap_run(c, prec, z, zn, v, vn, mu, c->p.post_smooth, c->p.nmr, false, R);
 }
@@ -667,7 +769,12 @@ static void normalise_fields(ddtm_ctx* c, float2* tv, int nv) {
   B.axpby(zero.data(), s, sc.data(), s);
 }
 
-void run_setup(ddtm_ctx* c, double mu, uint64_t seed) {
+// Adaptive setup (Sec. 2.6).  update = false: random test vectors, one SAP pass,
+// then n_setup - 1 inverse-iteration steps.  update = true (the HMC usage of
+// Sec. 3.2: the setup follows a changed gauge field or twist): the existing
+// test vectors are kept, P and the coarse operators are rebuilt from them and
+// n_iter inverse-iteration steps follow.
+void run_setup(ddtm_ctx* c, double mu, uint64_t seed, bool update = false, int n_iter = 0) {
   const FineGeom& g = c->g;
   const ddtm_params& p = c->p;
   int nv = p.nv[0];
@@ -675,7 +782,9 @@ void run_setup(ddtm_ctx* c, double mu, uint64_t seed) {
   size_t n = (size_t)g.V * 12;
   c->tv0.ensure((size_t)nv * n * sizeof(float2));
   float2* tv = c->tv0.as<float2>();
-  for (int i = 0; i < nv; i++) launch_gaussian(tv + (size_t)i * n, n, seed * 0x100000001b3ull + (uint64_t)i * (n * 2 + 17), c->stream);
+  if (!update)
+    for (int i = 0; i < nv; i++)
+      launch_gaussian(tv + (size_t)i * n, n, seed * 0x100000001b3ull + (uint64_t)i * (n * 2 + 17), c->stream);
   // the setup works in the smoother precision, FP32 for an FP64 smoother
   int sp = p.smoother_prec == PREC_F64 ? PREC_F32 : p.smoother_prec;
   size_t fb = fine_field_bytes(g, sp);
@@ -695,19 +804,64 @@ void run_setup(ddtm_ctx* c, double mu, uint64_t seed) {
   };
   float* bnp = sp == PREC_F16 ? bsn : nullptr;
   float* xnp = sp == PREC_F16 ? xsn : nullptr;
-  // k = 1: the SAP smoother on every random vector, all vectors as one batch
-  to_sp();
-  sap_run(c, sp, xs, xnp, bs, bnp, mu, p.post_smooth, p.nmr, true, nv);
-  from_sp();
-  normalise_fields(c, tv, nv);
-  build_hierarchy(c);
-  // k >= 2: one multigrid iteration per test vector, all vectors as one batch
-  for (int k = 2; k <= p.n_setup; k++) {
+  // level 1 of three: its own random vectors, batch-interleaved for the level-1 kernels
+  const bool three = p.n_levels == 3;
+  const int nv1 = three ? p.nv[1] : 0, R1 = three ? coarse_batch(nv1) : 0;
+  float2 *tv1 = nullptr, *b1 = nullptr, *x1 = nullptr;
+  size_t N1 = 0;
+  if (three) {
+    N1 = (size_t)g.Nb * 2 * nv;  // level-1 sites x n1
+    c->a1.nv = nv1;
+    c->a1.tv.ensure((size_t)nv1 * N1 * sizeof(float2));
+    tv1 = c->a1.tv.as<float2>();
+    if (!update)
+      for (int i = 0; i < nv1; i++)
+        launch_gaussian(tv1 + (size_t)i * N1, N1,
+                        (seed ^ 0x5bd1e995ull) * 0x100000001b3ull + (uint64_t)i * (N1 * 2 + 29), c->stream);
+    b1 = (float2*)c->scratch.get("setup_b1", N1 * R1 * sizeof(float2));
+    x1 = (float2*)c->scratch.get("setup_x1", N1 * R1 * sizeof(float2));
+  }
+  Blas B1(c->stream, &c->scratch);
+  auto normalise_l1 = [&]() {
+    for (int i = 0; i < nv1; i++) {
+      const double n2 = B1.norm2(tv1 + (size_t)i * N1, 1, N1);
+      const double sc = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+      B1.axpby(make_double2(sc, 0), tv1 + (size_t)i * N1, 1, make_double2(0, 0), tv1 + (size_t)i * N1, 1, N1);
+    }
+  };
+  if (update) {  // hierarchy from the kept test vectors
+    build_hierarchy(c);
+    if (three) build_hierarchy1(c);
+  } else {
+    // k = 1: the SAP smoother on every random vector, all vectors as one batch
+    to_sp();
+    sap_run(c, sp, xs, xnp, bs, bnp, mu, p.post_smooth, p.nmr, true, nv);
+    from_sp();
+    normalise_fields(c, tv, nv);
+    build_hierarchy(c);
+    if (three) {
+      launch_l1_transpose(tv1, b1, N1, nv1, R1, 0, c->stream);
+      sap_l1(c, (cplx<float>*)x1, (const cplx<float>*)b1, mu, p.post_smooth, p.nmr, true, R1);
+      launch_l1_transpose(tv1, x1, N1, nv1, R1, 1, c->stream);
+      normalise_l1();
+      build_hierarchy1(c);
+    }
+  }
+  // k >= 2: one multigrid iteration per test vector, all vectors as one batch (level by level)
+  const int k_last = update ? n_iter + 1 : p.n_setup;
+  for (int k = 2; k <= k_last; k++) {
     to_sp();
     mg_precondition(c, sp, xs, xnp, bs, bnp, mu, nv);
     from_sp();
     normalise_fields(c, tv, nv);
     build_hierarchy(c);
+    if (three) {
+      launch_l1_transpose(tv1, b1, N1, nv1, R1, 0, c->stream);
+      precondition_l1(c, (cplx<float>*)x1, (const cplx<float>*)b1, mu, R1);
+      launch_l1_transpose(tv1, x1, N1, nv1, R1, 1, c->stream);
+      normalise_l1();
+      build_hierarchy1(c);
+    }
   }
   CK(cudaStreamSynchronize(c->stream));
 }
@@ -735,9 +889,15 @@ static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-static void check_level(ddtm_ctx* c, int level, int lo) {
-  if (level < lo || level > 1) throw Error(DDTM_ERR_ARG, "level out of range for a two-level hierarchy");
-  (void)c;
+static void check_level(ddtm_ctx* c, int level, int lo, int hi_off = 0) {
+  if (level < lo || level > c->p.n_levels - 1 - hi_off)
+    throw Error(DDTM_ERR_ARG, "level " + std::to_string(level) + " out of range for a " +
+                                  std::to_string(c->p.n_levels) + "-level hierarchy");
+}
+static CoarseLevel& level_op(ddtm_ctx* c, int level) { return level == 2 ? c->c2 : c->c1; }
+static void check_tc_all(ddtm_ctx* c) {
+  check_tc_error(c->c1);
+  check_tc_error(c->c2);
 }
 
 extern "C" {
@@ -783,7 +943,25 @@ int ddtm_setup(ddtm_ctx* ctx, double mu, uint64_t seed) {
   double t0 = now_s();
   run_setup(ctx, mu, seed);
   CK(cudaStreamSynchronize(ctx->stream));
-  check_tc_error(ctx->c1);
+  check_tc_all(ctx);
+  ctx->setup_s = now_s() - t0;
+  ctx->setup_done = true;
+  ctx->setup_mu = mu;
+  API_END(ctx)
+}
+
+int ddtm_setup_update(ddtm_ctx* ctx, double mu, int n_iter) {
+  API_BEGIN(ctx)
+  require_gauge(ctx);
+  if (!std::isfinite(mu) || n_iter < 0) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  if (!ctx->tv0.p || ctx->nv0 != ctx->p.nv[0] ||
+      (ctx->p.n_levels == 3 && (!ctx->a1.tv.p || ctx->a1.nv != ctx->p.nv[1])))
+    throw Error(DDTM_ERR_STATE, "no test vectors of these parameters to update (call ddtm_setup first)");
+  invalidate_setup(ctx);
+  double t0 = now_s();
+  run_setup(ctx, mu, 0, true, n_iter);
+  CK(cudaStreamSynchronize(ctx->stream));
+  check_tc_all(ctx);
   ctx->setup_s = now_s() - t0;
   ctx->setup_done = true;
   ctx->setup_mu = mu;
@@ -794,8 +972,23 @@ int ddtm_set_test_vectors(ddtm_ctx* ctx, int level, const double* v, int nv, int
   API_BEGIN(ctx)
   require_gauge(ctx);
   check_loc(loc);
-  if (level != 0) throw Error(DDTM_ERR_ARG, "test vectors can be set for level 0 only");
-  if (!v || nv != ctx->p.nv[0]) throw Error(DDTM_ERR_ARG, "nv must equal params.nv[0]");
+  check_level(ctx, level, 0, 1);
+  if (!v || nv != ctx->p.nv[level]) throw Error(DDTM_ERR_ARG, "nv must equal params.nv[level]");
+  if (level == 1) {
+    // level-1 test vectors (canonical coarse vectors of level 1): P_1 and D_2
+    if (!ctx->have_P || !ctx->c1.built) throw Error(DDTM_ERR_STATE, "set the level-0 test vectors first");
+    const size_t N1 = (size_t)ctx->c1.Nc * ctx->c1.n;
+    ctx->a1.nv = nv;
+    ctx->a1.tv.ensure((size_t)nv * N1 * sizeof(float2));
+    for (int i = 0; i < nv; i++) {
+      const double* din = stage_in(ctx, "canon_cin", v + 2 * N1 * i, N1, loc);
+      launch_convert_complex(din, PREC_F32, ctx->a1.tv.as<float2>() + (size_t)i * N1, N1, ctx->stream);
+    }
+    build_hierarchy1(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->setup_done = true;
+    return DDTM_OK;
+  }
   size_t nsp = (size_t)ctx->g.V * 12;
   ctx->nv0 = nv;
   ctx->tv0.ensure((size_t)nv * nsp * sizeof(float2));
@@ -804,8 +997,9 @@ int ddtm_set_test_vectors(ddtm_ctx* ctx, int level, const double* v, int nv, int
     launch_spinor_from_canon(ctx->g, PREC_F32, ctx->tv0.as<float2>() + (size_t)i * nsp, nullptr, din, ctx->stream);
   }
   build_hierarchy(ctx);
+  if (ctx->p.n_levels == 3 && ctx->a1.tv.p && ctx->a1.nv == ctx->p.nv[1]) build_hierarchy1(ctx);
   CK(cudaStreamSynchronize(ctx->stream));
-  ctx->setup_done = true;
+  ctx->setup_done = ctx->p.n_levels == 2 || ctx->c2.built;
   API_END(ctx)
 }
 
@@ -814,6 +1008,10 @@ int ddtm_build_coarse(ddtm_ctx* ctx) {
   require_gauge(ctx);
   if (!ctx->tv0.p || ctx->nv0 <= 0) throw Error(DDTM_ERR_STATE, "no test vectors (call ddtm_setup)");
   build_hierarchy(ctx);
+  if (ctx->p.n_levels == 3) {
+    if (!ctx->a1.tv.p || ctx->a1.nv != ctx->p.nv[1]) throw Error(DDTM_ERR_STATE, "no level-1 test vectors");
+    build_hierarchy1(ctx);
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   API_END(ctx)
 }
@@ -835,8 +1033,25 @@ int ddtm_get_prolongator(ddtm_ctx* ctx, int level, double* W, int loc) {
 int ddtm_restrict(ddtm_ctx* ctx, int level, double* cout, const double* x, int nrhs, int loc) {
   API_BEGIN(ctx)
   check_loc(loc);
-  if (level != 0 || !cout || !x || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  if (!cout || !x || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  check_level(ctx, level, 0, 1);
   require_hierarchy(ctx);
+  if (level == 1) {  // level-1 vectors -> level-2 vectors, one at a time (R = 1 interleaved = canonical)
+    Blas B1(ctx->stream, &ctx->scratch);
+    const size_t n1 = (size_t)ctx->c1.Nc * ctx->c1.n, n2 = (size_t)ctx->c2.Nc * ctx->c2.n;
+    float2* v = (float2*)ctx->scratch.get("abi_l1", n1 * 8);
+    float2* c2 = (float2*)ctx->scratch.get("abi_l2", n2 * 8);
+    for (int r = 0; r < nrhs; r++) {
+      const double* din = stage_in(ctx, "canon_cin", x + 2 * n1 * r, n1, loc);
+      double* dout = stage_out(ctx, "canon_cout", cout + 2 * n2 * r, n2, loc);
+      B1.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), v, 1, n1);
+      launch_l1_restrict(ctx->a1, ctx->c1, c2, v, 1, 1, ctx->stream);
+      B1.axpby(make_double2(1, 0), c2, 1, make_double2(0, 0), dout, 0, n2);
+      unstage_out(ctx, cout + 2 * n2 * r, dout, n2, loc);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DDTM_OK;
+  }
   Blas B(ctx->stream, &ctx->scratch);
   const FineGeom& g = ctx->g;
   CoarseLevel& L = ctx->c1;
@@ -858,8 +1073,25 @@ int ddtm_restrict(ddtm_ctx* ctx, int level, double* cout, const double* x, int n
 int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* cin, int nrhs, int loc) {
   API_BEGIN(ctx)
   check_loc(loc);
-  if (level != 0 || !cin || !x || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  if (!cin || !x || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  check_level(ctx, level, 0, 1);
   require_hierarchy(ctx);
+  if (level == 1) {  // level-2 vectors -> level-1 vectors
+    Blas B1(ctx->stream, &ctx->scratch);
+    const size_t n1 = (size_t)ctx->c1.Nc * ctx->c1.n, n2 = (size_t)ctx->c2.Nc * ctx->c2.n;
+    float2* v = (float2*)ctx->scratch.get("abi_l1", n1 * 8);
+    float2* c2 = (float2*)ctx->scratch.get("abi_l2", n2 * 8);
+    for (int r = 0; r < nrhs; r++) {
+      const double* din = stage_in(ctx, "canon_cin", cin + 2 * n2 * r, n2, loc);
+      double* dout = stage_out(ctx, "canon_cout", x + 2 * n1 * r, n1, loc);
+      B1.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), c2, 1, n2);
+      launch_l1_prolong(ctx->a1, ctx->c1, v, c2, 1, 1, 0, ctx->stream);
+      B1.axpby(make_double2(1, 0), v, 1, make_double2(0, 0), dout, 0, n1);
+      unstage_out(ctx, x + 2 * n1 * r, dout, n1, loc);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DDTM_OK;
+  }
   Blas B(ctx->stream, &ctx->scratch);
   const FineGeom& g = ctx->g;
   CoarseLevel& L = ctx->c1;
@@ -881,10 +1113,11 @@ int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* cin, int nrh
 int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs, double mu, int loc) {
   API_BEGIN(ctx)
   check_loc(loc);
-  if (level != 1 || !x || !y || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments (coarse level is 1)");
+  if (!x || !y || nrhs < 0) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  check_level(ctx, level, 1);
   require_hierarchy(ctx);
   if (nrhs == 0) return DDTM_OK;
-  CoarseLevel& L = ctx->c1;
+  CoarseLevel& L = level_op(ctx, level);
   const size_t nc = (size_t)L.Nc * L.n;
   // all right-hand sides go through one batched stencil pass
   cplx<float>* xv = (cplx<float>*)ctx->scratch.get("abi_c32", nc * nrhs * 8);
@@ -921,13 +1154,41 @@ int ddtm_apply_Dc(ddtm_ctx* ctx, int level, double* y, const double* x, int nrhs
   API_END(ctx)
 }
 
+int ddtm_sap_coarse(ddtm_ctx* ctx, int level, double* x, const double* b, int nrhs, double mu, int ncycles, int nmr,
+                    int loc) {
+  API_BEGIN(ctx)
+  check_loc(loc);
+  if (!x || !b || nrhs < 0 || ncycles < 0 || nmr < 1 || !std::isfinite(mu)) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  if (ctx->p.n_levels != 3 || level != 1) throw Error(DDTM_ERR_ARG, "SAP on a coarse level exists for level 1 of three");
+  require_hierarchy(ctx);
+  if (nrhs == 0) return DDTM_OK;
+  CoarseLevel& L1 = ctx->c1;
+  const int Rc = (nrhs + 3) / 4 * 4;
+  const size_t nc = (size_t)L1.Nc * L1.n;
+  cplx<float>* bv = (cplx<float>*)ctx->scratch.get("abi_sapc_b", nc * Rc * 8);
+  cplx<float>* xv = (cplx<float>*)ctx->scratch.get("abi_sapc_x", nc * Rc * 8);
+  CK(cudaMemsetAsync(bv, 0, nc * Rc * 8, ctx->stream));
+  for (int r = 0; r < nrhs; r++) {
+    const double* din = stage_in(ctx, "canon_cin", b + 2 * nc * r, nc, loc);
+    launch_coarse_interleave(L1, bv, const_cast<double*>(din), r, Rc, 0, ctx->stream);
+  }
+  sap_l1(ctx, xv, bv, mu, ncycles, nmr, true, Rc);
+  for (int r = 0; r < nrhs; r++) {
+    double* dout = stage_out(ctx, "canon_cout", x + 2 * nc * r, nc, loc);
+    launch_coarse_interleave(L1, xv, dout, r, Rc, 1, ctx->stream);
+    unstage_out(ctx, x + 2 * nc * r, dout, nc, loc);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  API_END(ctx)
+}
+
 int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, int loc, int* iters) {
   API_BEGIN(ctx)
   check_loc(loc);
   if (!x || !b) throw Error(DDTM_ERR_ARG, "invalid arguments");
   require_hierarchy(ctx);
   Blas B(ctx->stream, &ctx->scratch);
-  CoarseLevel& L = ctx->c1;
+  CoarseLevel& L = coarsest(ctx);
   size_t nc = (size_t)L.Nc * L.n;
   cplx<float>* bv = (cplx<float>*)ctx->scratch.get("abi_c32", nc * 8);
   cplx<float>* xv = (cplx<float>*)ctx->scratch.get("abi_c32b", nc * 8);
@@ -1012,7 +1273,7 @@ int ddtm_solve(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu, i
     all_conv = all_conv && o.converged;
   }
   CK(cudaStreamSynchronize(ctx->stream));
-  check_tc_error(ctx->c1);
+  check_tc_all(ctx);
   acc.coarse_iters = ctx->coarse_iters;
   acc.solve_s = now_s() - t0;
   acc.setup_s = ctx->setup_s;
@@ -1042,6 +1303,13 @@ int ddtm_save_setup(ddtm_ctx* ctx, const char* path) {
                 ctx->nv0};
   bool ok = fwrite(MAGIC, 1, 8, f) == 8 && fwrite(hdr, sizeof(int), 9, f) == 9 &&
             fwrite(&ctx->setup_mu, sizeof(double), 1, f) == 1 && fwrite(host.data(), 1, bytes, f) == bytes;
+  if (ok && ctx->p.n_levels == 3) {  // level-1 test vectors: nv1, block[1], then nv1 level-1 vectors (FP32)
+    const size_t b1 = (size_t)ctx->a1.nv * ctx->c1.Nc * ctx->c1.n * sizeof(float2);
+    std::vector<char> h1(b1);
+    CK(cudaMemcpy(h1.data(), ctx->a1.tv.p, b1, cudaMemcpyDeviceToHost));
+    int h2[5] = {ctx->a1.nv, ctx->p.block[1][0], ctx->p.block[1][1], ctx->p.block[1][2], ctx->p.block[1][3]};
+    ok = fwrite(h2, sizeof(int), 5, f) == 5 && fwrite(h1.data(), 1, b1, f) == b1;
+  }
   fclose(f);
   if (!ok) throw Error(DDTM_ERR_ARG, std::string("short write to ") + path);
   API_END(ctx)
@@ -1068,12 +1336,29 @@ int ddtm_load_setup(ddtm_ctx* ctx, const char* path) {
   size_t bytes = (size_t)hdr[8] * ctx->g.V * 12 * sizeof(float2);
   std::vector<char> host(bytes);
   ok = fread(host.data(), 1, bytes, f) == bytes;
+  std::vector<char> h1;
+  if (ok && ctx->p.n_levels == 3) {
+    int h2[5];
+    ok = fread(h2, sizeof(int), 5, f) == 5 && h2[0] == ctx->p.nv[1];
+    for (int m = 0; ok && m < 4; m++) ok = h2[1 + m] == ctx->p.block[1][m];
+    if (ok) {
+      const size_t b1 = (size_t)h2[0] * ctx->g.Nb * 2 * hdr[8] * sizeof(float2);
+      h1.resize(b1);
+      ok = fread(h1.data(), 1, b1, f) == b1;
+    }
+  }
   fclose(f);
-  if (!ok) throw Error(DDTM_ERR_ARG, "truncated setup file");
+  if (!ok) throw Error(DDTM_ERR_ARG, "truncated setup file, or its level-1 part does not match the parameters");
   ctx->nv0 = hdr[8];
   ctx->tv0.ensure(bytes);
   CK(cudaMemcpyAsync(ctx->tv0.p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
   build_hierarchy(ctx);
+  if (ctx->p.n_levels == 3) {
+    ctx->a1.nv = ctx->p.nv[1];
+    ctx->a1.tv.ensure(h1.size());
+    CK(cudaMemcpyAsync(ctx->a1.tv.p, h1.data(), h1.size(), cudaMemcpyHostToDevice, ctx->stream));
+    build_hierarchy1(ctx);
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->setup_mu = mu;
   ctx->setup_done = true;

@@ -57,6 +57,7 @@ SIGNATURES = {
     "ddtm_set_params": (_I, [_P, ctypes.POINTER(ddtm_params)]),
     "ddtm_load_gauge": (_I, [_P, _P, _I, _D, _D]),
     "ddtm_apply_D": (_I, [_P, _P, _P, _I, _D, _I, _I]),
+    "ddtm_set_boundary_phases": (_I, [_P, ctypes.POINTER(_D)]),
     "ddtm_apply_D_noalloc": (_I, [_P, _P, _P, _D, _I]),
     "ddtm_sap": (_I, [_P, _P, _P, _I, _D, _I, _I, _I, _I]),
     "ddtm_field_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
@@ -66,6 +67,7 @@ SIGNATURES = {
     "ddtm_apply_D_field": (_I, [_P, _P, _P, _D]),
     "ddtm_sap_field": (_I, [_P, _P, _P, _D, _I, _I]),
     "ddtm_setup": (_I, [_P, _D, ctypes.c_uint64]),
+    "ddtm_setup_update": (_I, [_P, _D, _I]),
     "ddtm_set_test_vectors": (_I, [_P, _I, _P, _I, _I]),
     "ddtm_build_coarse": (_I, [_P]),
     "ddtm_get_prolongator": (_I, [_P, _I, _P, _I]),
@@ -73,6 +75,7 @@ SIGNATURES = {
     "ddtm_prolong": (_I, [_P, _I, _P, _P, _I, _I]),
     "ddtm_apply_Dc": (_I, [_P, _I, _P, _P, _I, _D, _I]),
     "ddtm_coarse_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I)]),
+    "ddtm_sap_coarse": (_I, [_P, _I, _P, _P, _I, _D, _I, _I, _I]),
     "ddtm_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(ddtm_solve_info)]),
     "ddtm_eo_cg": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, ctypes.POINTER(ddtm_solve_info)]),
     "ddtm_save_setup": (_I, [_P, ctypes.c_char_p]),
@@ -174,6 +177,12 @@ def ddtm_load_gauge(ctx, U, kappa, c_sw):
     _check(ctx, _lib.ddtm_load_gauge(ctx, pu, loc, kappa, c_sw))
 
 
+def ddtm_set_boundary_phases(ctx, theta):
+    """Twisted boundary conditions: psi(x + L_mu mu_hat) = exp(i theta[mu]) psi(x), mu = t, x, y, z."""
+    t = (_D * 4)(*[float(v) for v in theta])
+    _check(ctx, _lib.ddtm_set_boundary_phases(ctx, t))
+
+
 def ddtm_apply_D(ctx, y, x, nrhs, mu, prec):
     by, bx = _buf(y, True), _buf(x)
     _check(ctx, _lib.ddtm_apply_D(ctx, by[0], bx[0], nrhs, mu, prec, _same_loc(by, bx)))
@@ -225,6 +234,10 @@ def ddtm_setup(ctx, mu, seed):
     _check(ctx, _lib.ddtm_setup(ctx, mu, seed))
 
 
+def ddtm_setup_update(ctx, mu, n_iter):
+    _check(ctx, _lib.ddtm_setup_update(ctx, mu, n_iter))
+
+
 def ddtm_set_test_vectors(ctx, level, v, nv):
     p, loc = _buf(v)
     _check(ctx, _lib.ddtm_set_test_vectors(ctx, level, p, nv, loc))
@@ -252,6 +265,11 @@ def ddtm_prolong(ctx, level, x, c, nrhs):
 def ddtm_apply_Dc(ctx, level, y, x, nrhs, mu):
     by, bx = _buf(y, True), _buf(x)
     _check(ctx, _lib.ddtm_apply_Dc(ctx, level, by[0], bx[0], nrhs, mu, _same_loc(by, bx)))
+
+
+def ddtm_sap_coarse(ctx, level, x, b, nrhs, mu, ncycles, nmr):
+    bxx, bb = _buf(x, True), _buf(b)
+    _check(ctx, _lib.ddtm_sap_coarse(ctx, level, bxx[0], bb[0], nrhs, mu, ncycles, nmr, _same_loc(bxx, bb)))
 
 
 def ddtm_coarse_solve(ctx, x, b, mu_c):
