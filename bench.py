@@ -106,9 +106,7 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc, rhs=1.0):
 
 # DRAM traffic per unit from one ncu capture of the kernel as it stands (profiles/), scaled to a
 # launch of the bench workload by the units it processes; remove an entry when its kernel changes.
-NCU_TRAFFIC = {
-    "sap_half_f16": {"bytes_per_site_rhs": 1.0652e9 / (663552 / 2 * 12), "capture": "k_sap_half_24x24x24x48.md"},
-}
+NCU_TRAFFIC = {}
 
 
 def algorithmic_flops(name, V, Vb, b, nv, nmr, rhs_per_launch):
@@ -154,7 +152,7 @@ def parse_args():
     ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the oracle residual of the full-size solutions")
-    ap.add_argument("--study", choices=["eo-cg", "aggregation"], default=None,
+    ap.add_argument("--study", choices=["eo-cg", "aggregation", "levels"], default=None,
                     help="eo-cg: the even-odd CG baseline against DD-alpha-AMG, t_total = t_setup + n_rhs t_solve "
                          "(Sec. 3.1.2, Fig. 3); aggregation: block size x N_v sweep (Sec. 3.3, Table 4)")
     ap.add_argument("--oracle-units", default=None, help=argparse.SUPPRESS)  # child process of the CPU baseline
@@ -481,6 +479,35 @@ def study(args):
                                            "speedup": n * t_cg / (t_setup + n * t_rhs)} for n in (1, 12, 100)},
                     "model": "t_total(n) = t_setup + n t_solve (MG, solve per rhs from the 12-rhs batch) "
                              "against n t_cg (one CG solve per rhs)"})
+    elif args.study == "levels":
+        # two against three levels (4^4 then 2^4 aggregates, N_v 24 then 32): setup and one 12-rhs solve,
+        # with the per-kernel timers on (durations of each kernel family)
+        runs = []
+        for levels in (2, 3):
+            ctx = _mg_ctx(ddtm, dims, U, wl, stream=stream)
+            if levels == 3:
+                p = ddtm.ddtm_get_params(ctx)
+                p.n_levels, p.nv[1] = 3, 32
+                for m in range(4):
+                    p.block[1][m] = 2
+                ddtm.ddtm_set_params(ctx, p)
+            x = torch.zeros_like(b)
+            ddtm.ddtm_timer_reset(ctx)
+            ddtm.ddtm_timer_enable(ctx, True)
+            t_setup, _ = _timed(torch, stream, lambda: ddtm.ddtm_setup(ctx, mu, SEED))
+            rep_setup = ddtm.ddtm_timer_report(ctx)
+            ddtm.ddtm_timer_reset(ctx)
+            t_solve, (info, code) = _timed(torch, stream, lambda: ddtm.ddtm_solve(ctx, x, b, NRHS, mu))
+            rep_solve = ddtm.ddtm_timer_report(ctx)
+            ddtm.ddtm_timer_enable(ctx, False)
+            top = lambda rep: {k: round(v["ms"], 1) for k, v in sorted(rep.items(), key=lambda kv: -kv[1]["ms"])[:12]}
+            runs.append({"levels": levels, "setup_s": t_setup, "solve_s": t_solve, "outer_iters": info.iters,
+                         "coarse_rhs_iters": info.coarse_iters, "max_relres": info.max_relres,
+                         "converged": code == ddtm.OK, "setup_top_ms": top(rep_setup), "solve_top_ms": top(rep_solve),
+                         "launches_solve": sum(v["launches"] for v in rep_solve.values())})
+            ddtm.ddtm_destroy(ctx)
+            torch.cuda.empty_cache()
+        out["runs"] = runs
     else:
         runs = []
         for block in ((4, 4, 4, 4), (2, 2, 2, 2)):

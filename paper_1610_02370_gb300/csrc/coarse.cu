@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(cplx<float>* __restrict__ 
                                                        const cplx<float>* __restrict__ x_hop, const DS* __restrict__ Dc,
                                                        const int* __restrict__ tab, const int* __restrict__ osite, int nout,
                                                        int n, int nv, int R, int G, float mu_c, int mode, float sres,
-                                                       float sy) {
+                                                       float sy, int dsel) {
   const int np = n / 2, nch = R / RC, per = np * G, spb = blockDim.x / per;
   const int t = threadIdx.x, rp = t % np, g = (t / np) % G, q = t / per;
   const int idx = blockIdx.x * spb + q;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(cplx<float>* __restrict__ 
     }
   }
   if (mode & 2)
-    for (int d = 1; d < 9; d++) {
+    for (int d = dsel ? dsel : 1; d <= (dsel ? dsel : 8); d++) {  // dsel > 0: hop dsel - 1 only
       const int src = __ldg(tab + (size_t)(d - 1) * nout + idx);
       block_mv2<DS, RC>(Dc + ((size_t)site * 9 + d) * n * n + r0, x_hop + (size_t)src * n * R + c0, n, R, acc0, acc1);
     }
@@ -540,21 +540,27 @@ __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__
 template <typename DS, int RC>
 static void coarse_apply_t(const CoarseLevel& c, const CoarseShape& sh, cplx<float>* y, const cplx<float>* xs,
                            const cplx<float>* xh, const int* tab, const int* osite, int nout, int R, double mu_c, int mode,
-                           float sres, float sy, cudaStream_t st) {
+                           float sres, float sy, cudaStream_t st, int dsel) {
   unsigned grid = (unsigned)((nout + sh.spb - 1) / sh.spb);
   if (grid == 0) return;
   k_coarse_apply<DS, RC><<<grid, sh.threads, 0, st>>>(y, xs, xh, c.Dc.as<DS>(), tab, osite, nout, c.n, c.nv, R, sh.groups,
-                                                      (float)mu_c, mode, sres, sy);
+                                                      (float)mu_c, mode, sres, sy, dsel);
   CKL("coarse_apply");
 }
 
 template <typename DS>
 static void coarse_apply_d(const CoarseLevel& c, cplx<float>* y, const cplx<float>* xs, const cplx<float>* xh, const int* tab,
-                           const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st) {
+                           const int* osite, int nout, int R, double mu_c, int mode, float sres, float sy, cudaStream_t st,
+                           int dsel = 0) {
   const CoarseShape sh = coarse_shape(c.n, R);
-  if (sh.rc == 4) coarse_apply_t<DS, 4>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
-  else if (sh.rc == 2) coarse_apply_t<DS, 2>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
-  else coarse_apply_t<DS, 1>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st);
+  if (sh.rc == 4) coarse_apply_t<DS, 4>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st, dsel);
+  else if (sh.rc == 2) coarse_apply_t<DS, 2>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st, dsel);
+  else coarse_apply_t<DS, 1>(c, sh, y, xs, xh, tab, osite, nout, R, mu_c, mode, sres, sy, st, dsel);
+}
+
+void launch_coarse_apply_hop(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, int hop, cudaStream_t st) {
+  ScopedTimer timer_("coarse_apply", st, R);
+  coarse_apply_d<float2>(c, y, x, x, c.nbr.as<int>(), nullptr, c.Nc, R, 0.0, 2, 1.f, 0.f, st, hop + 1);
 }
 
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,

@@ -30,6 +30,8 @@ void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* D
 // full-lattice vectors: y = sy*y + sres * (mode&1: self + i mu_c Gamma5_c, mode&2: hops) x
 void launch_coarse_apply_full(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, double mu_c, int mode,
                               float sres, float sy, cudaStream_t st);
+// y = hop `hop` (0..7) of the stencil alone, through the neighbour table c.nbr
+void launch_coarse_apply_hop(const CoarseLevel& c, cplx<float>* y, const cplx<float>* x, int R, int hop, cudaStream_t st);
 // parity-compact: odd outputs, self term from x_o (compact odd), hops from x_e (compact even)
 void launch_coarse_apply_odd(const CoarseLevel& c, cplx<float>* y_o, const cplx<float>* x_o, const cplx<float>* x_e, int R,
                              double mu_c, int mode, float sres, float sy, cudaStream_t st);

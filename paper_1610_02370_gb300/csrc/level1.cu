@@ -398,7 +398,8 @@ void launch_l1_galerkin(const Level1Agg& a, const CoarseLevel& c1, CoarseLevel& 
   try {
     for (int d = 0; d < 9; d++) {
       view.nbr.p = (void*)(a.tabs.as<int>() + (size_t)d * 8 * c1.Nc);
-      launch_coarse_apply_full(view, (cplx<float>*)part, (const cplx<float>*)Phi, n2, 0.0, d == 0 ? 3 : 2, 1.f, 0.f, st);
+      if (d == 0) launch_coarse_apply_full(view, (cplx<float>*)part, (const cplx<float>*)Phi, n2, 0.0, 3, 1.f, 0.f, st);
+      else launch_coarse_apply_hop(view, (cplx<float>*)part, (const cplx<float>*)Phi, n2, d - 1, st);
       k_l1_project<<<blocks_for((long)a.Nagg * n2 * n2, 256), 256, 0, st>>>(c2.Dc.as<float2>(), part, a.P.as<float2>(),
                                                                            a.sites.as<int>(), a.Nagg, a.Vb, n1, a.nv, d);
       CKL("l1_project");
@@ -417,8 +418,9 @@ void launch_l1_sap_half(const Level1Agg& a, const CoarseLevel& c1, float2* x, co
   ScopedTimer timer_("l1_sap_half", st, R);
   if (!a.geom || a.Nagg < 2) throw Error(DDTM_ERR_STATE, "internal: level-1 aggregates not built");
   const int n = c1.n;
-  int Rch = R < 12 ? R : 12;
-  while (R % Rch) Rch -= 4;  // R is a multiple of 4 (coarse batches)
+  // chunks of 4 right-hand sides: a level-1 lattice has few aggregates (256 per colour at 32^3 x 64),
+  // so the chunks are what fills the GPU
+  const int Rch = 4;
   if (Rch < 4 || R % 4) throw Error(DDTM_ERR_ARG, "internal: level-1 SAP needs batches of a multiple of 4");
   const size_t smem = 2 * (size_t)a.Vb * n * Rch * sizeof(float2) + Rch * sizeof(float2) + 9 * (size_t)a.Vb * 4;
   if (smem > 220 * 1024) throw Error(DDTM_ERR_ARG, "level-1 SAP: block volume x dofs too large for shared memory");

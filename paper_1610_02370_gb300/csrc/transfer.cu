@@ -169,6 +169,80 @@ __global__ void k_restrict(cplx<float>* __restrict__ c, Spinor<PI> psi, size_t f
   }
 }
 
+// The same restriction with P read once per HC right-hand sides (the kernel
+// above reads it once per RC = 4): one CTA per block and chunk of HC
+// right-hand sides works through the
+// two chirality halves s in turn; for each it stages components 6s..6s+5 of the
+// chunk's block vectors in shared memory (FP32, [rc][6][Vb]: 72 KB for 6
+// right-hand sides at Vb = 256, so three CTAs share an SM), and warp w
+// computes OW outputs of half s at once (each staged entry read once serves OW outputs, each P entry HC
+// right-hand sides).  Every output is a sum over the block's 6 Vb entries in
+// the same order as k_restrict (lane partial sums over sites, then a warp sum).
+template <int PI, typename PS, int HC, int OW>
+__global__ void __launch_bounds__(256, 3) k_restrict_half(cplx<float>* __restrict__ c, Spinor<PI> psi, size_t fstride,
+                                                          long V, const PS* __restrict__ P, int nv, int R, int Rs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sp = reinterpret_cast<float2*>(smem_raw);  // [HC][6][Vb]
+  const int Vb = psi.Vb, blk = blockIdx.x, r0 = blockIdx.y * HC;
+  const int nr = R - r0 < HC ? R - r0 : HC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = 2 * nv;
+  for (int s = 0; s < 2; s++) {
+    if (s) __syncthreads();  // the previous half's reads are done
+    for (int rc = 0; rc < HC; rc++) {
+      Spinor<PI> f = psi;
+      f.d += (size_t)(r0 + rc) * fstride;
+      if (f.nrm) f.nrm += (size_t)(r0 + rc) * V;
+      for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
+        if (rc < nr) {
+          cplx<typename Prec<PI>::real> v[12];
+          f.load(blk, loc, v);
+#pragma unroll
+          for (int k = 0; k < 6; k++) {
+            const cplx<typename Prec<PI>::real> a = s ? v[6 + k] : v[k];  // constant register indices
+            sp[((size_t)rc * 6 + k) * Vb + loc] = make_float2((float)a.re, (float)a.im);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 6; k++) sp[((size_t)rc * 6 + k) * Vb + loc] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+    __syncthreads();
+    for (int i0 = w * OW; i0 < nv; i0 += nw * OW) {
+      cplx<float> acc[OW][HC];
+#pragma unroll
+      for (int u = 0; u < OW; u++)
+#pragma unroll
+        for (int rc = 0; rc < HC; rc++) acc[u][rc] = cplx<float>(0, 0);
+      for (int comp = 0; comp < 6; comp++)
+        for (int loc = lane; loc < Vb; loc += 32) {
+          cplx<float> pv[OW];
+#pragma unroll
+          for (int u = 0; u < OW; u++) {
+            const int i = i0 + u < nv ? i0 + u : nv - 1;
+            pv[u] = ldp<PS>(P + (((size_t)(blk * 2 + s) * nv + i) * 6 + comp) * Vb + loc);
+          }
+#pragma unroll
+          for (int rc = 0; rc < HC; rc++) {
+            const float2 f2 = sp[((size_t)rc * 6 + comp) * Vb + loc];
+            const cplx<float> fv(f2.x, f2.y);
+#pragma unroll
+            for (int u = 0; u < OW; u++) cmac_conj(acc[u][rc], pv[u], fv);
+          }
+        }
+#pragma unroll
+      for (int u = 0; u < OW; u++)
+#pragma unroll
+        for (int rc = 0; rc < HC; rc++) {
+          acc[u][rc].re = warp_sum(acc[u][rc].re);
+          acc[u][rc].im = warp_sum(acc[u][rc].im);
+          if (lane == 0 && rc < nr && i0 + u < nv) c[((size_t)blk * n + s * nv + i0 + u) * Rs + r0 + rc] = acc[u][rc];
+        }
+    }
+  }
+}
+
 // x_r = P e_r (add = 0) or x_r += P e_r (add = 1) for a batch of R fields; e
 // interleaved.  One CTA per block, thread = site; e_B (n x R) staged in shared
 // memory; each P entry loaded once per thread serves RC right-hand sides.
@@ -225,9 +299,18 @@ __global__ void k_prolong(Spinor<PO> x, size_t fstride, long V, const cplx<float
 
 static const int RST_RC = 4, PRO_RC = 2;
 
+static const int RH_C = 6, RH_OW = 3;  // right-hand sides per CTA, outputs per warp pass
 template <int PI, typename PS>
 static void restrict_p(const FineGeom& g, cplx<float>* c, Spinor<PI> f, size_t fstride, const PS* P, int nv, int R,
                        int Rs, cudaStream_t st) {
+  if (R > RST_RC && (size_t)RH_C * 6 * g.Vb * sizeof(float2) <= 200 * 1024) {
+    // several chunks of RST_RC would read P once per chunk: read it once per RH_C right-hand sides
+    const size_t smem = (size_t)RH_C * 6 * g.Vb * sizeof(float2);
+    set_dynamic_smem((const void*)k_restrict_half<PI, PS, RH_C, RH_OW>, smem);
+    dim3 grid(g.Nb, (R + RH_C - 1) / RH_C);
+    k_restrict_half<PI, PS, RH_C, RH_OW><<<grid, 256, smem, st>>>(c, f, fstride, g.V, P, nv, R, Rs);
+    return;
+  }
   size_t smem = (size_t)RST_RC * 12 * g.Vb * sizeof(cplx<float>);
   set_dynamic_smem((const void*)k_restrict<PI, PS, RST_RC>, 200 * 1024);
   dim3 grid(g.Nb, (R + RST_RC - 1) / RST_RC);

@@ -95,3 +95,4 @@ def test_sap_zero_cycles_and_field_api(lib):
             ddtm.ddtm_field_destroy(fx)
     finally:
         ddtm.ddtm_destroy(ctx)
+
