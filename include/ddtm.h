@@ -287,7 +287,8 @@ int ddtm_load_setup(ddtm_ctx* ctx, const char* path);
 
 /* ---- execution options ---------------------------------------------------------- */
 
-/* Set / read an execution option of the context (results do not depend on it):
+/* Set / read an execution option of the context (results depend on none but
+ * the test hook "tc_forced_timeout_us"):
  *   "graphs" (default 1): each iteration of the coarsest even-odd GMRES
  *     (Sec. 2.5; operator passes, Gram-Schmidt, Givens update, residual
  *     estimate) is captured once per iteration index, batch and buffer set
@@ -301,7 +302,14 @@ int ddtm_load_setup(ddtm_ctx* ctx, const char* path);
  *     and keeps the fastest for that shape; each output is formed by the same
  *     MMAs in the same order in every variant, so results do not change.
  *     0 uses the fixed rule (2 CTAs per SM up to 16 right-hand sides, else 1).
- * DDTM_ERR_ARG for an unknown name. */
+ *   "tc_forced_timeout_us" (default 0, process-wide; a test hook of the
+ *     failure path): when v > 0, the MMA thread of every tensor-core pass
+ *     first waits v microseconds on a barrier that nothing completes; the
+ *     wait runs out, the pass stops (its bulk copies awaited, tensor memory
+ *     freed) and the call reports DDTM_ERR_TIMEOUT with its outputs
+ *     undefined.  Passes so launched are neither autotuned nor captured into
+ *     graphs.  Valid range 0 ... 1000000; set 0 to resume normal operation.
+ * DDTM_ERR_ARG for an unknown name or a value out of range. */
 int ddtm_set_option(ddtm_ctx* ctx, const char* name, int value);
 int ddtm_get_option(ddtm_ctx* ctx, const char* name, int* value);
 /* The autotuner's choices so far as a JSON object (NUL-terminated, truncated

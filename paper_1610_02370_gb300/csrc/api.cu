@@ -385,6 +385,9 @@ int ddtm_set_option(ddtm_ctx* ctx, const char* name, int value) {
     ctx->use_graphs = value != 0;
   } else if (n == "autotune") {
     tc_autotune_enable(value != 0);
+  } else if (n == "tc_forced_timeout_us") {
+    if (value < 0 || value > 1000000) throw Error(DDTM_ERR_ARG, "tc_forced_timeout_us must lie in [0, 1000000]");
+    tc_set_forced_wait_ns((uint64_t)value * 1000ull);
   } else {
     throw Error(DDTM_ERR_ARG, "unknown option " + n);
   }
@@ -397,6 +400,7 @@ int ddtm_get_option(ddtm_ctx* ctx, const char* name, int* value) {
   const std::string n(name);
   if (n == "graphs") *value = ctx->use_graphs ? 1 : 0;
   else if (n == "graphs_cached") *value = (int)ctx->graphs.size();
+  else if (n == "tc_forced_timeout_us") *value = (int)(tc_forced_wait_ns() / 1000ull);
   else throw Error(DDTM_ERR_ARG, "unknown option " + n);
   API_END(ctx)
 }

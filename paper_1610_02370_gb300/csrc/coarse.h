@@ -88,6 +88,8 @@ void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t
 // autotuner of the tensor-core pass residency (process-wide): switch, and the
 // choices made so far as JSON {shape: {"ctas_per_sm": k, "ms": [t1, t2, ...]}}
 void tc_autotune_enable(bool on);
+void tc_set_forced_wait_ns(uint64_t ns);
+uint64_t tc_forced_wait_ns();
 std::string tc_autotune_report();
 // throws DDTM_ERR_TIMEOUT if a tensor-core pass gave up waiting (and clears the flag)
 void check_tc_error(CoarseLevel& c);

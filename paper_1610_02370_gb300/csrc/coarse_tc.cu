@@ -37,6 +37,8 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "coarse.h"
 #include "common.cuh"
 #include "ddtm_internal.h"
@@ -56,6 +58,9 @@ static const int TC_SMEM_3 = 70 * 1024;
 __host__ __device__ constexpr int tc_ctas_per_sm(int ngj) { return ngj <= 4 ? 2 : 1; }
 static int tc_smem_budget(int cps) { return cps >= 3 ? TC_SMEM_3 : cps == 2 ? TC_SMEM_2 : TC_SMEM_1; }
 static const uint64_t TC_WAIT_NS = 2000000000ull;
+// Test hook of the timeout path: when non-zero, every pass's MMA thread first waits this long on a
+// barrier that nothing completes (the wait runs out, the pass aborts, the API reports a timeout).
+static std::atomic<uint64_t> g_forced_wait_ns{0};
 
 __host__ __device__ __forceinline__ size_t img_off(int row, int k, int sbo) {
   return (size_t)(row >> 3) * sbo + (size_t)(k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
@@ -151,12 +156,13 @@ struct TcArgs {
   int kpad, sbo, a_bytes, b_bytes, ngj_all, bslot, apad, ns, nmma, tcols;
   uint32_t idesc;
   int* err;
+  uint64_t forced_wait_ns;  // > 0: the MMA thread first waits this long on a barrier nothing completes
 };
 
 template <int NGJ>
 __global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * TC_MAXNS + 5];
+  __shared__ __align__(8) uint64_t bars[2 * TC_MAXNS + 6];
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const Tc
   const uint32_t sB = sA + (uint32_t)(a.ns * a.a_bytes + a.apad);
   const uint32_t bar0 = ptx::smem_u32(bars);
   const uint32_t FULL = bar0, EMPTY = bar0 + 8u * TC_MAXNS, ACCF = bar0 + 16u * TC_MAXNS, ACCE = ACCF + 16u,
-                 FIN = ACCF + 32u;
+                 FIN = ACCF + 32u, NEVER = ACCF + 40u;
   volatile int* abort_flag = &abort_sh;
 
   if (threadIdx.x == 0) {
@@ -177,6 +183,7 @@ __global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const Tc
       ptx::mbar_init(ACCE + 8u * b, 4);
     }
     ptx::mbar_init(FIN, 1);
+    ptx::mbar_init(NEVER, 1);  // no thread arrives on it
     abort_sh = 0;
     ptx::fence_mbar_init();
   }
@@ -232,13 +239,16 @@ __global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const Tc
     }
     if (lane == 0) {
       // tail: every stage issued has landed (abort) or has been released by its MMAs
+      // (a stage released by its MMAs has landed; once a release wait gives up, the copies of that
+      // stage and of every later one are awaited directly)
       const uint32_t first = it > (uint32_t)a.ns ? it - (uint32_t)a.ns : 0u;
-      const bool ab = *abort_flag != 0;
+      bool ab = *abort_flag != 0;
       for (uint32_t k = first; k < it; k++) {
         const int s = (int)(k % (uint32_t)a.ns);
         const uint32_t ph = (k / (uint32_t)a.ns) & 1u;
-        if (ab) ptx::mbar_wait(FULL + 8u * s, ph, nullptr, TC_WAIT_NS / 8);
-        else ptx::mbar_wait(EMPTY + 8u * s, ph, abort_flag, TC_WAIT_NS);
+        if (!ab && ptx::mbar_wait(EMPTY + 8u * s, ph, abort_flag, TC_WAIT_NS)) continue;
+        ab = true;
+        ptx::mbar_wait(FULL + 8u * s, ph, nullptr, TC_WAIT_NS / 8);
       }
     }
     __syncwarp();
@@ -247,7 +257,9 @@ __global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const Tc
     if (lane == 0) {
       uint32_t it = 0;
       const int ksteps = a.kpad / 16;
-      for (int q = 0; q < nq; q++) {
+      // the forced wait can only run out: it raises the abort flag and no MMA is issued
+      const bool go = a.forced_wait_ns == 0 || ptx::mbar_wait(NEVER, 0u, abort_flag, a.forced_wait_ns);
+      for (int q = 0; go && q < nq; q++) {
         const int ab = q & 1;
         const uint32_t aph = ((uint32_t)q >> 1) & 1u;
         if (!ptx::mbar_wait(ACCE + 8u * ab, aph ^ 1u, abort_flag, TC_WAIT_NS)) break;
@@ -432,6 +444,9 @@ TcTune& tune() {
 
 void tc_autotune_enable(bool on) { tune().on = on; }
 
+void tc_set_forced_wait_ns(uint64_t ns) { g_forced_wait_ns.store(ns); }
+uint64_t tc_forced_wait_ns() { return g_forced_wait_ns.load(); }
+
 std::string tc_autotune_report() {
   TcTune& t = tune();
   std::lock_guard<std::mutex> lock(t.m);
@@ -469,7 +484,8 @@ void launch_coarse_tc(const CoarseLevel& c, const TcPass& p, int R, cudaStream_t
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(st, &cap));
   const bool idempotent = !(p.y && p.yin && p.sy != 0.f);
-  if (chosen || !t.on || cap != cudaStreamCaptureStatusNone || !idempotent || p.nout <= 0 || timer_on()) {
+  if (chosen || !t.on || cap != cudaStreamCaptureStatusNone || !idempotent || p.nout <= 0 || timer_on() ||
+      g_forced_wait_ns.load()) {
     launch_coarse_tc_cps(c, p, R, st, chosen);
     return;
   }
@@ -560,6 +576,7 @@ static void launch_coarse_tc_cps(const CoarseLevel& c, const TcPass& p, int R, c
     a.tcols = tc;
     a.idesc = ptx::idesc_f16_f32(128, nmma);
     a.err = c.tc_err.as<int>();
+    a.forced_wait_ns = g_forced_wait_ns.load();
     const size_t smem = (size_t)a.ns * (a.a_bytes + a.bslot) + a.apad + 1024;
     const int grid = p.nout < cps * num_sms() ? p.nout : cps * num_sms();
 #define TC_LAUNCH(K)                                                                                    \

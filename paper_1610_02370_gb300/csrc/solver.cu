@@ -191,7 +191,7 @@ typedef std::function<void(cplx<float>*, const void*, int)> OpF32;
 // must name everything the launches' arguments depend on besides device
 // buffers (their addresses are fixed within a generation).
 static void run_as_graph(ddtm_ctx* c, const std::string& key, cudaStream_t* bst, const std::function<void()>& body) {
-  if (!c->use_graphs || timer_on()) {
+  if (!c->use_graphs || timer_on() || tc_forced_wait_ns()) {  // a forced tensor-core timeout is never captured
     body();
     return;
   }

@@ -153,3 +153,38 @@ def test_tc_two_level_solve_12rhs(lib):
             lib.ddtm_destroy(ctx)
     print("outer iterations F32 / F16 coarse:", iters)
     assert iters[lib.PREC_F16] <= iters[lib.PREC_F32] + 3
+
+
+def test_tc_forced_timeout_reports_status(lib, eo_case):
+    """Failure path of the bounded pipeline waits of the tensor-core stencil.
+    With the test hook on, the MMA thread of every pass first waits on a barrier
+    that nothing completes; the wait runs out after 2 ms, the pass stops (its
+    bulk copies awaited, tensor memory freed) and the call reports
+    DDTM_ERR_TIMEOUT.  The context stays usable: with the hook off, the same
+    call gives the same bits as before the timeout, and matches the oracle."""
+    c = eo_case
+    cl = c.cop.lat
+    nrhs, mu = 12, 0.05
+    x = synth.gaussian_vectors((nrhs,) + cl + (2 * c.nv,), seed=21).cuda()
+    y0 = torch.zeros_like(x)
+    lib.ddtm_apply_Dc(c.ctx, 1, y0, x, nrhs, mu)
+    lib.ddtm_set_option(c.ctx, "tc_forced_timeout_us", 2000)
+    try:
+        assert lib.ddtm_get_option(c.ctx, "tc_forced_timeout_us") == 2000
+        y1 = torch.zeros_like(x)
+        with pytest.raises(lib.DDTMError) as e:
+            lib.ddtm_apply_Dc(c.ctx, 1, y1, x, nrhs, mu)
+        assert e.value.code == lib.ERR_TIMEOUT, str(e.value)
+    finally:
+        lib.ddtm_set_option(c.ctx, "tc_forced_timeout_us", 0)
+    assert lib.ddtm_get_option(c.ctx, "tc_forced_timeout_us") == 0
+    y2 = torch.zeros_like(x)
+    lib.ddtm_apply_Dc(c.ctx, 1, y2, x, nrhs, mu)
+    assert torch.equal(y0, y2)
+    y2 = y2.cpu().numpy()
+    for r in range(nrhs):
+        want = c.cop.apply(x[r].cpu().numpy(), mu)
+        assert relerr(y2[r], want) < 2e-3, (r, relerr(y2[r], want))
+    for bad in (-1, 1000001):
+        with pytest.raises(lib.DDTMError):
+            lib.ddtm_set_option(c.ctx, "tc_forced_timeout_us", bad)
