@@ -601,7 +601,10 @@ def main():
     mu = wl["mu"]
     info_last = {}
 
+    nstep = [0]
+
     def step():
+        t0 = time.time()
         ddtm.ddtm_setup(ctx, mu, SEED)
         for sgn in twists:  # one setup serves both flavours (+mu and -mu)
             info, code = ddtm.ddtm_solve(ctx, x, b, NRHS, sgn * mu)
@@ -609,6 +612,13 @@ def main():
                 raise RuntimeError("solve did not converge: " + ddtm.ddtm_last_error(ctx))
             info_last.update(iters=info.iters, restarts=info.restarts, coarse_iters=info.coarse_iters,
                              max_relres=info.max_relres, solve_s=info.solve_s, setup_s=info.setup_s)
+            if rank == 0:  # progress on stderr (the JSON line stays alone on stdout)
+                sys.stderr.write("[bench] step %d mu %+g: %d outer iterations, %d coarse, relres %.2e, "
+                                 "setup %.2f s, solve %.2f s, wall %.1f s\n"
+                                 % (nstep[0], sgn * mu, info.iters, info.coarse_iters, info.max_relres,
+                                    info.setup_s, info.solve_s, time.time() - t0))
+                sys.stderr.flush()
+        nstep[0] += 1
 
     for _ in range(args.warmup):
         step()

@@ -6,12 +6,25 @@
 // Layouts and type tags are described in blas.h.
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "blas.h"
 #include "common.cuh"
 #include "ddtm_internal.h"
 #include "timer.h"
 
+#ifndef DDTM_DOTS_EPT
+#define DDTM_DOTS_EPT 4
+#endif
+#ifndef DDTM_MAXPY_UNROLL
+#define DDTM_MAXPY_UNROLL 4
+#endif
+
 namespace ddtm {
+
+static constexpr int MAXPY_UNROLL = DDTM_MAXPY_UNROLL;  // basis vectors in flight per multi-axpy step
 
 template <typename T> __device__ __forceinline__ double2 ld2(const T* p, size_t i);
 template <> __device__ __forceinline__ double2 ld2<float2>(const float2* p, size_t i) { float2 a = p[i]; return make_double2(a.x, a.y); }
@@ -108,33 +121,103 @@ __global__ void k_bdots(const TV* __restrict__ V, size_t ldv, int nvec, const TW
   }
 }
 
-// Interleaved FP32 sets with an even number R of right-hand sides: a thread
-// reads 16-byte pairs (two consecutive right-hand sides of one entry) of w
-// once per JB basis vectors and of each of those vectors; partial as k_bdots.
-// blockDim is a multiple of R/2 and the chunks are multiples of blockDim, so a
-// thread always holds the same pair of right-hand sides.
-template <int JB, typename TV>
+// Separate sets (one contiguous vector per right-hand side): CTA (c, g, r)
+// reads its chunk of w(., r) once and forms the inner products with basis
+// vectors g JB ... g JB + JB - 1 of rhs r, so w is read once per JB vectors
+// (not once per vector); partial[(j R + r) G + c].
+template <typename TV, typename TW, int JB>
+__global__ void __launch_bounds__(256) k_bdots_sep(const TV* __restrict__ V, size_t ldv, int nvec,
+                                                    const TW* __restrict__ w, size_t n, int R,
+                                                    double2* __restrict__ partial) {
+  __shared__ double red[8][2 * JB];  // per warp (blockDim <= 256)
+  const int G = gridDim.x, j0 = blockIdx.y * JB, r = blockIdx.z, bd = blockDim.x, t = threadIdx.x;
+  const int nj = nvec - j0 < JB ? nvec - j0 : JB;
+  const size_t chunk = ((n + (size_t)G * bd - 1) / ((size_t)G * bd)) * bd;
+  const size_t beg = (size_t)blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+  const TV* Vr = V + (size_t)j0 * ldv + (size_t)r * n;
+  const TW* wr = w + (size_t)r * n;
+  typedef typename Acc<TV, TW>::T AT;
+  AT are[JB], aim[JB];
+#pragma unroll
+  for (int jj = 0; jj < JB; jj++) are[jj] = aim[jj] = 0;
+#pragma unroll 2
+  for (size_t i = beg + t; i < end; i += bd) {
+    const auto y = ldc<AT>(wr, i);
+#pragma unroll
+    for (int jj = 0; jj < JB; jj++) {
+      if (jj < nj) {
+        const auto x = ldc<AT>(Vr + (size_t)jj * ldv, i);
+        are[jj] += x.re * y.re + x.im * y.im;
+        aim[jj] += x.re * y.im - x.im * y.re;
+      }
+    }
+  }
+  const int wi = t >> 5, nw = bd >> 5;
+#pragma unroll
+  for (int jj = 0; jj < JB; jj++) {
+    const double a = warp_sum((double)are[jj]), b = warp_sum((double)aim[jj]);
+    if ((t & 31) == 0) {
+      red[wi][2 * jj] = a;
+      red[wi][2 * jj + 1] = b;
+    }
+  }
+  __syncthreads();
+  if (t < nj) {
+    double a = 0, b = 0;
+    for (int k = 0; k < nw; k++) {
+      a += red[k][2 * t];
+      b += red[k][2 * t + 1];
+    }
+    partial[((size_t)(j0 + t) * R + r) * G + blockIdx.x] = make_double2(a, b);
+  }
+}
+
+// Interleaved FP32 sets with an even number R of right-hand sides, read in
+// 16-byte pairs (two consecutive right-hand sides of one entry).  Work comes
+// in spans of EPT x blockDim consecutive pairs: thread t of a CTA takes pairs
+// base + t + u blockDim (u < EPT) of its span, so for each basis vector a CTA
+// reads one contiguous piece of EPT x blockDim pairs (long DRAM bursts rather
+// than a short segment of every vector), and a thread always holds the same
+// pair of right-hand sides (blockDim and the spans are multiples of R/2).
+// CTA c takes spans c, c + G, ... (G = gridDim.x, sized so that every CTA gets
+// the same number of spans and one wave of resident CTAs holds them all).
+
+// Multi-dot: CTA (c, g) sweeps its spans of w against basis vectors
+// g JB ... g JB + JB - 1 and writes one partial per (vector, rhs):
+// partial[(j R + r) G + c].
+template <int JB, int EPT, typename TV>
 __global__ void __launch_bounds__(256) k_bdots_pairs(const TV* __restrict__ V, size_t ldv, int nvec,
                                                       const float4* __restrict__ w, size_t npairs, int R,
                                                       double2* __restrict__ partial) {
   extern __shared__ float red_s[];  // [blockDim][4 JB + 1]
   const int G = gridDim.x, j0 = blockIdx.y * JB, Rh = R / 2, bd = blockDim.x, t = threadIdx.x;
   const int nj = nvec - j0 < JB ? nvec - j0 : JB;
+  const size_t span = (size_t)bd * EPT;
   float acc[JB][4];
 #pragma unroll
   for (int jj = 0; jj < JB; jj++) acc[jj][0] = acc[jj][1] = acc[jj][2] = acc[jj][3] = 0.f;
-  const size_t chunk = ((npairs + (size_t)G * bd - 1) / ((size_t)G * bd)) * bd;
-  const size_t beg = (size_t)blockIdx.x * chunk, end = beg + chunk < npairs ? beg + chunk : npairs;
-  for (size_t i = beg + t; i < end; i += bd) {
-    const float4 y = __ldg(w + i);
+  for (size_t base = (size_t)blockIdx.x * span; base < npairs; base += (size_t)G * span) {
+    float4 y[EPT];
+    bool in[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; u++) {
+      const size_t i = base + t + (size_t)u * bd;
+      in[u] = i < npairs;
+      y[u] = in[u] ? __ldg(w + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
     for (int jj = 0; jj < JB; jj++) {
       if (jj < nj) {
-        const float4 x = ld_pair(V + (size_t)(j0 + jj) * ldv, i);
-        acc[jj][0] += x.x * y.x + x.y * y.y;
-        acc[jj][1] += x.x * y.y - x.y * y.x;
-        acc[jj][2] += x.z * y.z + x.w * y.w;
-        acc[jj][3] += x.z * y.w - x.w * y.z;
+        const TV* vj = V + (size_t)(j0 + jj) * ldv;
+#pragma unroll
+        for (int u = 0; u < EPT; u++) {
+          if (!in[u]) continue;
+          const float4 x = ld_pair(vj, base + t + (size_t)u * bd);
+          acc[jj][0] += x.x * y[u].x + x.y * y[u].y;
+          acc[jj][1] += x.x * y[u].y - x.y * y[u].x;
+          acc[jj][2] += x.z * y[u].z + x.w * y[u].w;
+          acc[jj][3] += x.z * y[u].w - x.w * y[u].z;
+        }
       }
     }
   }
@@ -156,9 +239,13 @@ __global__ void __launch_bounds__(256) k_bdots_pairs(const TV* __restrict__ V, s
 }
 
 // w(., r) += sign * sum_j coef[j * R + r] V_j(., r) for interleaved FP32 w with
-// an even number of right-hand sides, V FP32 or FP16: 16-byte pairs of w, EPT
-// pairs per thread, the basis loop outside; optional per-rhs squared norms of
-// the result in npartial[r * G + cta].
+// an even number of right-hand sides, V FP32 or FP16: CTA c takes the
+// contiguous units [c U / G, (c + 1) U / G) of U = npairs / (R/2) units of R/2
+// pairs (balanced to a unit, a thread always on the same pair of right-hand
+// sides), one 16-byte pair of w per thread and step with the basis loop inside
+// (MAXPY_UNROLL vectors in flight); optional per-rhs squared norms of the
+// result in npartial[r * G + cta].  (Spans of several pairs per thread, as in
+// the multi-dot, measured slower here: more registers, fewer resident CTAs.)
 template <typename TV>
 __global__ void __launch_bounds__(256) k_bmaxpy_pairs(float2* __restrict__ w, const TV* __restrict__ V, size_t ldv,
                                                        int nvec, const double2* __restrict__ coef, size_t npairs, int R,
@@ -166,43 +253,28 @@ __global__ void __launch_bounds__(256) k_bmaxpy_pairs(float2* __restrict__ w, co
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sc = reinterpret_cast<float2*>(smem_raw);  // [nvec][R], times sign
   __shared__ double2 red[256];
-  const int G = gridDim.x, bd = blockDim.x, Rh = R / 2, q = threadIdx.x % Rh;
-  for (int k = threadIdx.x; k < nvec * R; k += bd) sc[k] = make_float2(sign * (float)coef[k].x, sign * (float)coef[k].y);
+  const int G = gridDim.x, bd = blockDim.x, Rh = R / 2, t = threadIdx.x, q = t % Rh;
+  for (int k = t; k < nvec * R; k += bd) sc[k] = make_float2(sign * (float)coef[k].x, sign * (float)coef[k].y);
   __syncthreads();
-  const int EPT = 4;
-  const size_t span = (size_t)bd * EPT;
+  const float4* sc4 = reinterpret_cast<const float4*>(sc);  // (coef of rhs 2q, coef of rhs 2q + 1) of vector j
+  const size_t nunits = npairs / Rh;
+  const size_t beg = nunits * blockIdx.x / G * Rh, end = nunits * (blockIdx.x + 1) / G * Rh;
   float4* w4 = reinterpret_cast<float4*>(w);
   float nn0 = 0.f, nn1 = 0.f;
-  for (size_t base = (size_t)blockIdx.x * span; base < npairs; base += (size_t)G * span) {
-    float4 acc[EPT];
-    bool in[EPT];
-#pragma unroll
-    for (int u = 0; u < EPT; u++) {
-      const size_t i = base + threadIdx.x + (size_t)u * bd;
-      in[u] = i < npairs;
-      acc[u] = in[u] ? w4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll 2
+  for (size_t i = beg + t; i < end; i += bd) {
+    float4 acc = w4[i];
+#pragma unroll (MAXPY_UNROLL)
     for (int j = 0; j < nvec; j++) {
-      const TV* vj = V + (size_t)j * ldv;
-      const float2 c0 = sc[j * R + 2 * q], c1 = sc[j * R + 2 * q + 1];
-#pragma unroll
-      for (int u = 0; u < EPT; u++) {
-        if (!in[u]) continue;
-        const float4 v = ld_pair(vj, base + threadIdx.x + (size_t)u * bd);
-        acc[u].x += c0.x * v.x - c0.y * v.y;
-        acc[u].y += c0.x * v.y + c0.y * v.x;
-        acc[u].z += c1.x * v.z - c1.y * v.w;
-        acc[u].w += c1.x * v.w + c1.y * v.z;
-      }
+      const float4 c = sc4[j * Rh + q];
+      const float4 v = ld_pair(V + (size_t)j * ldv, i);
+      acc.x += c.x * v.x - c.y * v.y;
+      acc.y += c.x * v.y + c.y * v.x;
+      acc.z += c.z * v.z - c.w * v.w;
+      acc.w += c.z * v.w + c.w * v.z;
     }
-#pragma unroll
-    for (int u = 0; u < EPT; u++) {
-      if (!in[u]) continue;
-      w4[base + threadIdx.x + (size_t)u * bd] = acc[u];
-      nn0 += acc[u].x * acc[u].x + acc[u].y * acc[u].y;
-      nn1 += acc[u].z * acc[u].z + acc[u].w * acc[u].w;
-    }
+    w4[i] = acc;
+    nn0 += acc.x * acc.x + acc.y * acc.y;
+    nn1 += acc.z * acc.z + acc.w * acc.w;
   }
   if (npartial) {
     red[threadIdx.x] = make_double2(nn0, nn1);
@@ -245,8 +317,8 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
   const int ncoef = INTER ? nvec * R : nvec;
   for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = INTER ? coef[k] : coef[(size_t)k * R + r_sep];
   __syncthreads();
-  double nn = 0;
   typedef typename Acc<TV, TW>::T AT;
+  AT nn = 0;  // squared norm of this thread's entries, in the arithmetic precision
   // each thread updates EPT entries spaced by the CTA size (coalesced), with
   // the basis loop outside so EPT independent loads are in flight per step
   const int EPT = 4;
@@ -280,11 +352,11 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
         if (!in[u]) continue;
         size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
         st2(w, i, acc[u].re, acc[u].im);
-        nn += (double)(acc[u].re * acc[u].re + acc[u].im * acc[u].im);
+        nn += acc[u].re * acc[u].re + acc[u].im * acc[u].im;
       }
     }
     if (npartial) {
-      double2 s = rhs_reduce(make_double2(nn, 0), R, red);
+      double2 s = rhs_reduce(make_double2((double)nn, 0), R, red);
       if ((int)threadIdx.x < R) npartial[(size_t)threadIdx.x * G + blockIdx.x] = s;
     }
   } else {
@@ -318,11 +390,11 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
         if (!in[u]) continue;
         size_t i = base + threadIdx.x + (size_t)u * blockDim.x;
         st2(wr, i, acc[u].re, acc[u].im);
-        nn += (double)(acc[u].re * acc[u].re + acc[u].im * acc[u].im);
+        nn += acc[u].re * acc[u].re + acc[u].im * acc[u].im;
       }
     }
     if (npartial) {
-      double2 s = cta_reduce(make_double2(nn, 0), reinterpret_cast<double*>(red));
+      double2 s = cta_reduce(make_double2((double)nn, 0), reinterpret_cast<double*>(red));
       if (threadIdx.x == 0) npartial[(size_t)r_sep * G + blockIdx.x] = s;
     }
   }
@@ -333,16 +405,38 @@ __global__ void k_bmaxpy(TW* __restrict__ w, const TV* __restrict__ V, size_t ld
 // thread keeps one right-hand side; separate sets: grid.y = right-hand side.
 template <typename TX, typename TY, bool INTER>
 __global__ void k_baxpby(const double2* __restrict__ a, const TX* x, const double2* __restrict__ b, TY* y, size_t n, int R) {
+  // arithmetic in the wider of the two storage precisions; 4 independent entries per thread and step
+  typedef typename Acc<TX, TY>::T AT;
   const int r = INTER ? (int)(threadIdx.x % R) : blockIdx.y;
   const double2 ca = a[r], cb = b[r];
-  const bool ra = ca.x != 0 || ca.y != 0, rb = cb.x != 0 || cb.y != 0;
+  const bool ra = ca.x != 0 || ca.y != 0, rb = cb.x != 0 || cb.y != 0, unit_b = cb.x == 1 && cb.y == 0;
+  const AT ar = (AT)ca.x, ai = (AT)ca.y, br = (AT)cb.x, bi = (AT)cb.y;
   const size_t N = INTER ? n * R : n;
   const size_t off = INTER ? 0 : (size_t)r * n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    double2 u = ra ? ld2(x, off + i) : make_double2(0, 0), v = rb ? ld2(y, off + i) : make_double2(0, 0);
-    double re = ca.x * u.x - ca.y * u.y + cb.x * v.x - cb.y * v.y;
-    double im = ca.x * u.y + ca.y * u.x + cb.x * v.y + cb.y * v.x;
-    st2(y, off + i, re, im);
+  const size_t bd = blockDim.x, stride = (size_t)gridDim.x * bd * 4;
+  for (size_t i0 = (size_t)blockIdx.x * bd * 4 + threadIdx.x; i0 < N; i0 += stride) {
+    cplx<AT> u[4], v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const size_t i = i0 + (size_t)k * bd;
+      const bool in = i < N;
+      u[k] = in && ra ? ldc<AT>(x, off + i) : cplx<AT>(0, 0);
+      v[k] = in && rb ? ldc<AT>(y, off + i) : cplx<AT>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const size_t i = i0 + (size_t)k * bd;
+      if (i >= N) break;
+      AT re, im;
+      if (unit_b) {  // y + a x: the common update, two fused multiply-adds per component
+        re = v[k].re + ar * u[k].re - ai * u[k].im;
+        im = v[k].im + ar * u[k].im + ai * u[k].re;
+      } else {
+        re = ar * u[k].re - ai * u[k].im + br * v[k].re - bi * v[k].im;
+        im = ar * u[k].im + ai * u[k].re + br * v[k].im + bi * v[k].re;
+      }
+      st2(y, off + i, re, im);
+    }
   }
 }
 
@@ -354,9 +448,19 @@ __global__ void k_bscale(const double2* __restrict__ a, const TX* x, TY* y, size
   const AT cr = (AT)a[r].x, ci = (AT)a[r].y;
   const size_t N = INTER ? n * R : n;
   const size_t off = INTER ? 0 : (size_t)r * n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    cplx<AT> u = ldc<AT>(x, off + i);
-    st2(y, off + i, cr * u.re - ci * u.im, cr * u.im + ci * u.re);
+  const size_t bd = blockDim.x, stride = (size_t)gridDim.x * bd * 4;
+  for (size_t i0 = (size_t)blockIdx.x * bd * 4 + threadIdx.x; i0 < N; i0 += stride) {
+    cplx<AT> u[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const size_t i = i0 + (size_t)k * bd;
+      u[k] = i < N ? ldc<AT>(x, off + i) : cplx<AT>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const size_t i = i0 + (size_t)k * bd;
+      if (i < N) st2(y, off + i, cr * u[k].re - ci * u[k].im, cr * u[k].im + ci * u[k].re);
+    }
   }
 }
 
@@ -443,7 +547,38 @@ static double set_bytes(const VSet& v) {
 }
 static const char* fam(const VSet& w, const char* coarse, const char* fine) { return w.inter ? coarse : fine; }
 
-static const int DOTS_JB = 8;
+// basis vectors per multi-dot CTA; pairs per thread and span of the multi-dot
+static const int DOTS_JB = 8, DOTS_EPT = DDTM_DOTS_EPT;
+
+// CTAs of a kernel the GPU holds at once for a block size and dynamic shared
+// memory (cached per kernel and shape).
+static int resident_ctas(const void* kernel, int bd, size_t smem) {
+  static std::mutex m;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  const auto key = std::make_tuple(kernel, bd, smem);
+  {
+    std::lock_guard<std::mutex> lock(m);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int dev = 0, sms = 0, per = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, bd, smem));
+  const int n = (per < 1 ? 1 : per) * sms;
+  std::lock_guard<std::mutex> lock(m);
+  cache[key] = n;
+  return n;
+}
+// CTAs for S spans when each CTA of `groups` grid rows is resident at once: as many rounds of
+// spans as needed, the same number of spans per CTA
+static int span_grid(size_t spans, int groups, int cap) {
+  const size_t per_row = (size_t)(cap / groups < 1 ? 1 : cap / groups);
+  const size_t rounds = (spans + per_row - 1) / per_row;
+  const size_t g = (spans + rounds - 1) / rounds;
+  return (int)(g < 1 ? 1 : g);
+}
+
 template <typename TV>
 static void maxpy_pairs_t(const VSet& w, const VSet& V, size_t ldv, int nvec, const double2* coef_dev, double sign,
                           double2* npart, int G, int bd, cudaStream_t st) {
@@ -458,37 +593,55 @@ static void launch_maxpy_pairs(const VSet& w, const VSet& V, size_t ldv, int nve
   if (V.type == 2) maxpy_pairs_t<__half2>(w, V, ldv, nvec, coef_dev, sign, npart, G, bd, st);
   else maxpy_pairs_t<float2>(w, V, ldv, nvec, coef_dev, sign, npart, G, bd, st);
 }
-static int maxpy_pairs_grid(const VSet& w, int bd) {
-  size_t npairs = w.n * w.R / 2, g = (npairs + (size_t)bd * 4 - 1) / ((size_t)bd * 4);
-  return (int)(g < 1 ? 1 : (g > 16384 ? 16384 : g));
+// one wave of resident CTAs, each taking at least one pair per thread (and at least one unit)
+static int maxpy_pairs_grid(const VSet& w, const VSet& V, int nvec, int bd) {
+  const void* k = V.type == 2 ? (const void*)k_bmaxpy_pairs<__half2> : (const void*)k_bmaxpy_pairs<float2>;
+  const size_t npairs = w.n * w.R / 2, units = npairs / (size_t)(w.R / 2);
+  size_t g = (size_t)resident_ctas(k, bd, (size_t)nvec * w.R * sizeof(float2)), cap = npairs / (size_t)bd;
+  if (g > cap) g = cap;
+  if (g > units) g = units;
+  return (int)(g < 1 ? 1 : g);
 }
 static bool pairs_ok(const VSet& V, size_t ldv, const VSet& w) {
   return w.inter && (V.type == 1 || V.type == 2) && w.type == 1 && w.R % 2 == 0 && lcm32(w.R / 2) <= 256 &&
          ldv % 2 == 0 && ((uintptr_t)V.p & 15) == 0 && ((uintptr_t)w.p & 15) == 0;
 }
 static int pairs_block(const VSet& w) { return inter_block(w.R / 2); }
-// CTAs along the vector: about 1200 CTAs in all (8 per SM) whatever the
-// number of basis blocks, each thread taking at least 4 pairs
-static int pairs_grid(const VSet& w, int bd, int nvec) {
-  const size_t npairs = w.n * w.R / 2, jb = (size_t)(nvec + 7) / 8;
-  size_t g = (1216 + jb - 1) / jb, gmax = npairs / ((size_t)bd * 4);
-  if (g > gmax) g = gmax;
-  return (int)(g < 1 ? 1 : g);
+static size_t dots_pairs_smem(int bd) { return (size_t)bd * (4 * DOTS_JB + 1) * sizeof(float); }
+static int pairs_grid(const VSet& w, const VSet& V, int bd, int nvec) {
+  const void* k = V.type == 2 ? (const void*)k_bdots_pairs<DOTS_JB, DOTS_EPT, __half2>
+                              : (const void*)k_bdots_pairs<DOTS_JB, DOTS_EPT, float2>;
+  const size_t npairs = w.n * w.R / 2, span = (size_t)bd * DOTS_EPT;
+  const int groups = (nvec + DOTS_JB - 1) / DOTS_JB;
+  return span_grid((npairs + span - 1) / span, groups, resident_ctas(k, bd, dots_pairs_smem(bd)));
 }
 template <typename TV>
 static void dots_pairs_t(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* partial, int G, int bd,
                          cudaStream_t st) {
-  const size_t smem = (size_t)bd * (4 * DOTS_JB + 1) * sizeof(float);
-  set_dynamic_smem((const void*)k_bdots_pairs<DOTS_JB, TV>, 64 * 1024);
+  set_dynamic_smem((const void*)k_bdots_pairs<DOTS_JB, DOTS_EPT, TV>, 64 * 1024);
   dim3 grid(G, (nvec + DOTS_JB - 1) / DOTS_JB);
-  k_bdots_pairs<DOTS_JB, TV><<<grid, bd, smem, st>>>((const TV*)V.p, ldv, nvec, (const float4*)w.p,
-                                                     w.n * w.R / 2, w.R, partial);
+  k_bdots_pairs<DOTS_JB, DOTS_EPT, TV><<<grid, bd, dots_pairs_smem(bd), st>>>(
+      (const TV*)V.p, ldv, nvec, (const float4*)w.p, w.n * w.R / 2, w.R, partial);
   CKL("bdots_pairs");
 }
 static void launch_dots_pairs(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* partial, int G, int bd,
                               cudaStream_t st) {
   if (V.type == 2) dots_pairs_t<__half2>(V, ldv, nvec, w, partial, G, bd, st);
   else dots_pairs_t<float2>(V, ldv, nvec, w, partial, G, bd, st);
+}
+
+static const int SEP_JB = 4;  // basis vectors per CTA of the separate-set multi-dot
+// separate-set multi-dot: about four waves of 256-thread CTAs over the (vector group, rhs) rows,
+// each CTA taking at least 4 entries per thread
+static int sep_grid(const VSet& w, int bd, int nvec) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t rows = (size_t)((nvec + SEP_JB - 1) / SEP_JB) * w.R;
+  size_t g = (size_t)4 * 8 * sms / rows, gmax = w.n / ((size_t)bd * 4);
+  if (g > gmax) g = gmax;
+  if (g > 512) g = 512;
+  return (int)(g < 1 ? 1 : g);
 }
 
 void Blas::dots(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out_host) {
@@ -498,7 +651,7 @@ void Blas::dots(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out
   if (nvec <= 0) return;
   const bool pairs = pairs_ok(V, ldv, w);
   int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
-  int G = pairs ? pairs_grid(w, bd, nvec) : grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  int G = pairs ? pairs_grid(w, V, bd, nvec) : w.inter ? grid_for(w.n * R, bd, 512) : sep_grid(w, bd, nvec);
   double2* partial = (double2*)pool->get("blas_partial", (size_t)nvec * R * G * sizeof(double2));
   double2* dres = (double2*)pool->get("blas_result", (size_t)nvec * R * sizeof(double2));
   dim3 grid(G, w.inter ? nvec : nvec * R);
@@ -510,7 +663,8 @@ void Blas::dots(const VSet& V, size_t ldv, int nvec, const VSet& w, double2* out
                    (k_bdots<A, B, true><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
   else
     DISPATCH_TYPES(V.type, w.type,
-                   (k_bdots<A, B, false><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
+                   (k_bdots_sep<A, B, SEP_JB><<<dim3(G, (nvec + SEP_JB - 1) / SEP_JB, R), bd, 0, st>>>(
+                       (const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
   CKL("bdots");
   k_reduce_partials<<<nvec * R, 128, 0, st>>>(partial, G, dres);
   CKL("reduce_partials");
@@ -542,7 +696,7 @@ void Blas::maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const doubl
   const int R = w.R;
   const bool pairs = pairs_ok(V, ldv, w);
   int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
-  int G = pairs ? maxpy_pairs_grid(w, bd) : maxpy_grid(w.inter ? w.n * R : w.n, bd);
+  int G = pairs ? maxpy_pairs_grid(w, V, nvec, bd) : maxpy_grid(w.inter ? w.n * R : w.n, bd);
   const double2* dc = coef_to_device(this, coef_host, (size_t)nvec * R, "blas_coef");
   double2* npart = norms2_host ? (double2*)pool->get("blas_npartial", (size_t)R * G * sizeof(double2)) : nullptr;
   size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
@@ -568,16 +722,25 @@ void Blas::maxpy(const VSet& w, const VSet& V, size_t ldv, int nvec, const doubl
   }
 }
 
+// 4 entries per thread and step (k_baxpby, k_bscale); at most about two waves of CTAs in all, so
+// each thread strides over many steps instead of the GPU scheduling short-lived CTAs
 static void elementwise_grid(const VSet& y, int* bd, dim3* grid) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const size_t cap = (size_t)16 * sms;  // CTAs in all
   if (y.inter) {
     *bd = inter_block(y.R);
-    size_t g = (y.n * y.R + *bd - 1) / *bd;
-    grid->x = (unsigned)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+    size_t g = (y.n * y.R + (size_t)*bd * 4 - 1) / ((size_t)*bd * 4);
+    grid->x = (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
     grid->y = 1;
   } else {
     *bd = 256;
-    size_t g = (y.n + 255) / 256;
-    grid->x = (unsigned)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+    size_t g = (y.n + 1023) / 1024, capr = cap / (size_t)y.R < 1 ? 1 : cap / (size_t)y.R;
+    grid->x = (unsigned)(g < 1 ? 1 : (g > capr ? capr : g));
     grid->y = y.R;
   }
   grid->z = 1;
@@ -606,7 +769,7 @@ void Blas::dots_dev(const VSet& V, size_t ldv, int nvec, const VSet& w, double2*
   if (nvec <= 0) return;
   const bool pairs = pairs_ok(V, ldv, w);
   int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
-  int G = pairs ? pairs_grid(w, bd, nvec) : grid_for(w.inter ? w.n * R : w.n, bd, 512);
+  int G = pairs ? pairs_grid(w, V, bd, nvec) : w.inter ? grid_for(w.n * R, bd, 512) : sep_grid(w, bd, nvec);
   double2* partial = (double2*)pool->get("blas_partial_dev", (size_t)nvec * R * G * sizeof(double2));
   dim3 grid(G, w.inter ? nvec : nvec * R);
   if (grid.y > 65535) throw Error(DDTM_ERR_ARG, "internal: too many vectors in one inner-product batch");
@@ -617,7 +780,8 @@ void Blas::dots_dev(const VSet& V, size_t ldv, int nvec, const VSet& w, double2*
                    (k_bdots<A, B, true><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
   else
     DISPATCH_TYPES(V.type, w.type,
-                   (k_bdots<A, B, false><<<grid, bd, 0, st>>>((const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
+                   (k_bdots_sep<A, B, SEP_JB><<<dim3(G, (nvec + SEP_JB - 1) / SEP_JB, R), bd, 0, st>>>(
+                       (const A*)V.p, ldv, nvec, (const B*)w.p, w.n, R, partial)));
   CKL("bdots");
   k_reduce_partials<<<nvec * R, 128, 0, st>>>(partial, G, out_dev);
   CKL("reduce_partials");
@@ -629,7 +793,7 @@ void Blas::maxpy_dev(const VSet& w, const VSet& V, size_t ldv, int nvec, const d
   const int R = w.R;
   const bool pairs = pairs_ok(V, ldv, w);
   int bd = pairs ? pairs_block(w) : w.inter ? inter_block(R) : 256;
-  int G = pairs ? maxpy_pairs_grid(w, bd) : maxpy_grid(w.inter ? w.n * R : w.n, bd);
+  int G = pairs ? maxpy_pairs_grid(w, V, nvec, bd) : maxpy_grid(w.inter ? w.n * R : w.n, bd);
   double2* npart = norms2_dev ? (double2*)pool->get("blas_npartial_dev", (size_t)R * G * sizeof(double2)) : nullptr;
   size_t smem = (size_t)(w.inter ? nvec * R : nvec) * sizeof(double2);
   if (smem > 200 * 1024) throw Error(DDTM_ERR_ARG, "internal: coefficient block too large");

@@ -65,6 +65,9 @@ void invalidate_setup(ddtm_ctx* c) {
 // the level whose operator the even-odd GMRES of Sec. 2.5 inverts (with the shifted twist)
 static CoarseLevel& coarsest(ddtm_ctx* c) { return c->p.n_levels == 3 ? c->c2 : c->c1; }
 
+// right-hand sides per batch of the level-0 transfers of the C ABI
+static const int ABI_BATCH = 12;
+
 void sap_run(ddtm_ctx* c, int prec, void* x, float* xn, const void* b, const float* bn, double mu, int ncycles, int nmr,
              bool from_zero, int R) {
   ensure_fine_prec(c, prec);
@@ -1052,19 +1055,26 @@ int ddtm_restrict(ddtm_ctx* ctx, int level, double* cout, const double* x, int n
     CK(cudaStreamSynchronize(ctx->stream));
     return DDTM_OK;
   }
-  Blas B(ctx->stream, &ctx->scratch);
+  // batches of up to ABI_BATCH right-hand sides go through one restriction launch (the solver's
+  // batched kernels, here with the FP32 P)
   const FineGeom& g = ctx->g;
   CoarseLevel& L = ctx->c1;
   size_t nsp = (size_t)g.V * 12, nc = (size_t)L.Nc * L.n;
-  float2* f = (float2*)ctx->scratch.get("abi_f32", nsp * 8);
-  cplx<float>* cv = (cplx<float>*)ctx->scratch.get("abi_c32", nc * 8);
-  for (int r = 0; r < nrhs; r++) {
-    const double* din = stage_in(ctx, "canon_in", x + 2 * nsp * r, nsp, loc);
-    double* dout = stage_out(ctx, "canon_cout", cout + 2 * nc * r, nc, loc);
-    launch_spinor_from_canon(g, PREC_F32, f, nullptr, din, ctx->stream);
-    launch_restrict(g, PREC_F32, cv, f, nullptr, ctx->P0.p, PREC_F32, L.nv, 1, 1, ctx->stream);
-    B.axpby(make_double2(1, 0), cv, 1, make_double2(0, 0), dout, 0, nc);
-    unstage_out(ctx, cout + 2 * nc * r, dout, nc, loc);
+  const int CH = nrhs < ABI_BATCH ? nrhs : ABI_BATCH;
+  float2* f = (float2*)ctx->scratch.get("abi_f32", (size_t)CH * nsp * 8);
+  cplx<float>* cv = (cplx<float>*)ctx->scratch.get("abi_c32", (size_t)CH * nc * 8);
+  for (int r0 = 0; r0 < nrhs; r0 += CH) {
+    const int R = nrhs - r0 < CH ? nrhs - r0 : CH;
+    for (int rc = 0; rc < R; rc++) {
+      const double* din = stage_in(ctx, "canon_in", x + 2 * nsp * (r0 + rc), nsp, loc);
+      launch_spinor_from_canon(g, PREC_F32, f + (size_t)rc * nsp, nullptr, din, ctx->stream);
+    }
+    launch_restrict(g, PREC_F32, cv, f, nullptr, ctx->P0.p, PREC_F32, L.nv, R, R, ctx->stream);
+    for (int rc = 0; rc < R; rc++) {
+      double* dout = stage_out(ctx, "canon_cout", cout + 2 * nc * (r0 + rc), nc, loc);
+      launch_coarse_interleave(L, cv, dout, rc, R, 1, ctx->stream);
+      unstage_out(ctx, cout + 2 * nc * (r0 + rc), dout, nc, loc);
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   API_END(ctx)
@@ -1092,19 +1102,24 @@ int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* cin, int nrh
     CK(cudaStreamSynchronize(ctx->stream));
     return DDTM_OK;
   }
-  Blas B(ctx->stream, &ctx->scratch);
   const FineGeom& g = ctx->g;
   CoarseLevel& L = ctx->c1;
   size_t nsp = (size_t)g.V * 12, nc = (size_t)L.Nc * L.n;
-  float2* f = (float2*)ctx->scratch.get("abi_f32", nsp * 8);
-  cplx<float>* cv = (cplx<float>*)ctx->scratch.get("abi_c32", nc * 8);
-  for (int r = 0; r < nrhs; r++) {
-    const double* din = stage_in(ctx, "canon_cin", cin + 2 * nc * r, nc, loc);
-    double* dout = stage_out(ctx, "canon_out", x + 2 * nsp * r, nsp, loc);
-    B.axpby(make_double2(1, 0), din, 0, make_double2(0, 0), cv, 1, nc);
-    launch_prolong(g, PREC_F32, f, nullptr, cv, ctx->P0.p, PREC_F32, L.nv, 1, 1, 0, ctx->stream);
-    launch_spinor_to_canon(g, PREC_F32, f, nullptr, dout, ctx->stream);
-    unstage_out(ctx, x + 2 * nsp * r, dout, nsp, loc);
+  const int CH = nrhs < ABI_BATCH ? nrhs : ABI_BATCH;
+  float2* f = (float2*)ctx->scratch.get("abi_f32", (size_t)CH * nsp * 8);
+  cplx<float>* cv = (cplx<float>*)ctx->scratch.get("abi_c32", (size_t)CH * nc * 8);
+  for (int r0 = 0; r0 < nrhs; r0 += CH) {
+    const int R = nrhs - r0 < CH ? nrhs - r0 : CH;
+    for (int rc = 0; rc < R; rc++) {
+      const double* din = stage_in(ctx, "canon_cin", cin + 2 * nc * (r0 + rc), nc, loc);
+      launch_coarse_interleave(L, cv, const_cast<double*>(din), rc, R, 0, ctx->stream);
+    }
+    launch_prolong(g, PREC_F32, f, nullptr, cv, ctx->P0.p, PREC_F32, L.nv, R, R, 0, ctx->stream);
+    for (int rc = 0; rc < R; rc++) {
+      double* dout = stage_out(ctx, "canon_out", x + 2 * nsp * (r0 + rc), nsp, loc);
+      launch_spinor_to_canon(g, PREC_F32, f + (size_t)rc * nsp, nullptr, dout, ctx->stream);
+      unstage_out(ctx, x + 2 * nsp * (r0 + rc), dout, nsp, loc);
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   API_END(ctx)

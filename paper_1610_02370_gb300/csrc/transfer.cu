@@ -104,10 +104,39 @@ __global__ void k_build_P(float2* __restrict__ P, const float2* __restrict__ tv,
   }
 }
 
+// Each CTA re-reads its aggregate half (nv x 6 x Vb complex FP32) from L2 in every Gram-Schmidt
+// step; when more CTAs run at once than L2 can hold the halves of, those re-reads go to HBM.  The
+// residency per SM is therefore capped (by reserving unused dynamic shared memory) so that the halves
+// of all resident CTAs take about BP_L2_BYTES: 3 CTAs per SM for nv = 24 and 4^4 aggregates (at
+// 32^3 x 64: 28.4 ms per build, against 29.4 ms with the 5 per SM the registers allow and 34.4 ms
+// with 2 per SM, which cuts the HBM traffic tenfold but leaves too few warps to hide L2 latency).
+#ifndef DDTM_BP_L2_MB
+#define DDTM_BP_L2_MB 136
+#endif
+static const size_t BP_L2_BYTES = (size_t)DDTM_BP_L2_MB << 20;
+
 void launch_build_P(const FineGeom& g, float2* P, const float2* tv, int nv, cudaStream_t st) {
   ScopedTimer timer_("build_P", st, nv);
   int threads = ((g.Vb + 31) / 32) * 32;
-  k_build_P<<<g.Nb * 2, threads, 0, st>>>(P, tv, nv, g.Vb, g.V);
+  int dev = 0, sms = 0, smem_sm = 0, smem_blk = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  CK(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  CK(cudaFuncGetAttributes(&fa, (const void*)k_build_P));
+  const size_t half = (size_t)nv * 6 * g.Vb * sizeof(float2);
+  size_t per_sm = (BP_L2_BYTES + half * sms / 2) / (half * (size_t)sms);  // rounded
+  size_t smem = 0;
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm < 8) {
+    // at most per_sm CTAs per SM: each reserves its share of the SM's shared memory, less its
+    // static shared memory and the 1 KB per CTA the runtime keeps
+    smem = (size_t)smem_sm / per_sm - 1024 - fa.sharedSizeBytes;
+    if (smem + fa.sharedSizeBytes > (size_t)smem_blk) smem = (size_t)smem_blk - fa.sharedSizeBytes;
+    set_dynamic_smem((const void*)k_build_P, smem);
+  }
+  k_build_P<<<g.Nb * 2, threads, smem, st>>>(P, tv, nv, g.Vb, g.V);
   CKL("build_P");
 }
 
@@ -297,7 +326,83 @@ __global__ void k_prolong(Spinor<PO> x, size_t fstride, long V, const cplx<float
   }
 }
 
+// The same prolongation with P read once per HC right-hand sides (the kernel
+// above reads it once per PRO_RC = 2): one CTA per block and chunk of HC
+// right-hand sides, thread = site.  The 6 x HC components of chirality half
+// s = 0 are formed in registers and parked in shared memory ([HC][6][Vb],
+// each thread its own site), those of s = 1 are formed next, and the site's 12
+// components of each right-hand side are stored together (FP16 storage keeps
+// one scale per site).  Every component is the same sum, in the same order,
+// as in k_prolong, so the results are identical.
+template <int PO, typename PS, int HC>
+__global__ void __launch_bounds__(256, 2) k_prolong_half(Spinor<PO> x, size_t fstride, long V, const cplx<float>* __restrict__ e,
+                                                         const PS* __restrict__ P, int nv, int R, int Rs, int add) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typedef typename Prec<PO>::real Rl;
+  const int Vb = x.Vb, blk = blockIdx.x, n = 2 * nv, r0 = blockIdx.y * HC;
+  const int nr = R - r0 < HC ? R - r0 : HC;
+  float2* park = reinterpret_cast<float2*>(smem_raw);                       // [HC][6][Vb]
+  cplx<float>* se = reinterpret_cast<cplx<float>*>(park + (size_t)HC * 6 * Vb);  // [n][HC]
+  for (int k = threadIdx.x; k < n * HC; k += blockDim.x) {
+    const int o = k / HC, rc = k - o * HC;
+    se[k] = rc < nr ? e[((size_t)blk * n + o) * Rs + r0 + rc] : cplx<float>(0, 0);
+  }
+  __syncthreads();
+  for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
+#pragma unroll 1
+    for (int s = 0; s < 2; s++) {
+      cplx<float> acc[HC][6];
+#pragma unroll
+      for (int rc = 0; rc < HC; rc++)
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[rc][c] = cplx<float>(0, 0);
+      for (int i = 0; i < nv; i++) {
+        const PS* col = P + ((size_t)(blk * 2 + s) * nv + i) * 6 * Vb + loc;
+        cplx<float> pv[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) pv[c] = ldp<PS>(col + (size_t)c * Vb);
+#pragma unroll
+        for (int rc = 0; rc < HC; rc++) {
+          const cplx<float> ev = se[(s * nv + i) * HC + rc];
+#pragma unroll
+          for (int c = 0; c < 6; c++) cmac(acc[rc][c], pv[c], ev);
+        }
+      }
+      if (s == 0) {
+#pragma unroll
+        for (int rc = 0; rc < HC; rc++)
+#pragma unroll
+          for (int c = 0; c < 6; c++) park[((size_t)rc * 6 + c) * Vb + loc] = make_float2(acc[rc][c].re, acc[rc][c].im);
+      } else {
+#pragma unroll
+        for (int rc = 0; rc < HC; rc++) {
+          if (rc >= nr) break;
+          Spinor<PO> f = x;
+          f.d += (size_t)(r0 + rc) * fstride;
+          if (f.nrm) f.nrm += (size_t)(r0 + rc) * V;
+          cplx<Rl> out[12];
+          if (add) f.loadw(blk, loc, out);
+#pragma unroll
+          for (int k = 0; k < 12; k++) {
+            cplx<float> a;
+            if (k < 6) {
+              const float2 v = park[((size_t)rc * 6 + k) * Vb + loc];
+              a = cplx<float>(v.x, v.y);
+            } else {
+              a = acc[rc][k - 6];
+            }
+            const cplx<Rl> ar((Rl)a.re, (Rl)a.im);
+            out[k] = add ? out[k] + ar : ar;
+          }
+          f.store(blk, loc, out);
+        }
+      }
+    }
+  }
+}
+
 static const int RST_RC = 4, PRO_RC = 2;
+static const int PH_C = 6;  // right-hand sides per CTA of k_prolong_half
 
 static const int RH_C = 6, RH_OW = 3;  // right-hand sides per CTA, outputs per warp pass
 template <int PI, typename PS>
@@ -327,12 +432,31 @@ static void restrict_t(const FineGeom& g, int pin, cplx<float>* c, const void* p
   CKL("restrict");
 }
 
+template <int PO, typename PS>
+static void prolong_half_p(const FineGeom& g, Spinor<PO> x, size_t fs, const cplx<float>* e, const PS* P, int nv, int R,
+                           int Rs, int add, size_t smem, cudaStream_t st) {
+  set_dynamic_smem((const void*)k_prolong_half<PO, PS, PH_C>, smem);
+  dim3 grid(g.Nb, (R + PH_C - 1) / PH_C);
+  const int threads = g.Vb < 256 ? ((g.Vb + 31) / 32) * 32 : 256;
+  k_prolong_half<PO, PS, PH_C><<<grid, threads, smem, st>>>(x, fs, g.V, e, P, nv, R, Rs, add);
+}
+
 template <typename PS>
 static void prolong_t(const FineGeom& g, int pout, void* x, float* xn, const cplx<float>* e, const PS* P, int nv, int R,
                       int Rs, int add, cudaStream_t st) {
   size_t smem = (size_t)2 * nv * Rs * sizeof(cplx<float>);
   int threads = g.Vb < 128 ? ((g.Vb + 31) / 32) * 32 : 128;
   size_t fs = (size_t)g.V * 12;
+  const size_t hsmem = (size_t)PH_C * 6 * g.Vb * sizeof(float2) + (size_t)2 * nv * PH_C * sizeof(cplx<float>);
+  if (R > PRO_RC && pout != PREC_F64 && hsmem <= 100 * 1024) {
+    // several chunks of PRO_RC would read P once per chunk: read it once per PH_C right-hand sides
+    if (pout == PREC_F32)
+      prolong_half_p<PREC_F32, PS>(g, Spinor<PREC_F32>{(float2*)x, nullptr, g.Vb}, fs, e, P, nv, R, Rs, add, hsmem, st);
+    else
+      prolong_half_p<PREC_F16, PS>(g, Spinor<PREC_F16>{(__half2*)x, xn, g.Vb}, fs, e, P, nv, R, Rs, add, hsmem, st);
+    CKL("prolong");
+    return;
+  }
   if (pout == PREC_F64)
     k_prolong<PREC_F64, PS, PRO_RC><<<g.Nb, threads, smem, st>>>(Spinor<PREC_F64>{(double2*)x, nullptr, g.Vb}, fs, g.V, e,
                                                                  P, nv, R, Rs, add);

@@ -87,6 +87,41 @@ def test_restrict_prolong_match_oracle(lib, case8):
     assert relerr(f.cpu().numpy(), want) < 2e-6
 
 
+@pytest.fixture(scope="module")
+def case24t(lib):
+    c = Case(lib, (16, 8, 8, 8), (4, 4, 4, 4), 0.3, 0.13, 1.2, 24, lib.PREC_F32, seed=7)
+    yield c
+    lib.ddtm_destroy(c.ctx)
+
+
+@pytest.mark.parametrize("nrhs", [5, 12, 13])
+def test_restrict_prolong_batched(lib, case24t, nrhs):
+    """Batches of right-hand sides through one restriction / prolongation launch
+    (P read once per 6 right-hand sides; 13 = a batch of 12 and a batch of 1):
+    each rhs equals, bit for bit, the same rhs transferred alone (same sums in
+    the same order), and matches the oracle's R = P^dagger and P (Sec. 2.3)."""
+    c = case24t
+    cl = c.cop.lat
+    psi = synth.gaussian_spinor(c.dims, seed=21, nrhs=nrhs)
+    cv = torch.zeros((nrhs,) + cl + (2 * c.nv,), dtype=torch.complex128, device="cuda")
+    lib.ddtm_restrict(c.ctx, 0, cv, psi.cuda(), nrhs)
+    e = synth.gaussian_vectors((nrhs,) + cl + (2 * c.nv,), seed=22)
+    f = torch.zeros_like(psi).cuda()
+    lib.ddtm_prolong(c.ctx, 0, f, e.cuda(), nrhs)
+    for r in range(nrhs):
+        c1 = torch.zeros_like(cv[r:r + 1])
+        lib.ddtm_restrict(c.ctx, 0, c1, psi[r:r + 1].contiguous().cuda(), 1)
+        assert torch.equal(cv[r:r + 1], c1), r
+        f1 = torch.zeros_like(f[r:r + 1])
+        lib.ddtm_prolong(c.ctx, 0, f1, e[r:r + 1].contiguous().cuda(), 1)
+        assert torch.equal(f[r:r + 1], f1), r
+    for r in (0, nrhs - 1):
+        want = aggregation.restrict(c.W, psi[r].numpy(), c.op.lat, c.block)
+        assert relerr(cv[r].cpu().numpy(), want) < 2e-6
+        want = aggregation.prolong(c.W, e[r].numpy(), c.op.lat, c.block)
+        assert relerr(f[r].cpu().numpy(), want) < 2e-6
+
+
 @pytest.mark.parametrize("mu", [0.01, -0.25])
 def test_coarse_operator_matches_oracle(lib, case8, mu):
     c = case8
