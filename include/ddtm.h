@@ -253,6 +253,14 @@ int ddtm_sap_coarse(ddtm_ctx* ctx, int level, double* x, const double* b, int nr
  * iteration count.  Returns DDTM_ERR_NOCONV if the tolerance was not reached. */
 int ddtm_coarse_solve(ddtm_ctx* ctx, double* x, const double* b, double mu_c, int loc, int* iters);
 
+/* The same solve for nrhs right-hand sides at once (arrays of nrhs canonical
+ * coarse vectors, contiguous): one batched GMRES whose Krylov kernels and
+ * coarse-stencil passes take all of them together, as inside the multigrid
+ * solver (the batch is padded with zero columns to the sizes those kernels
+ * take).  *iters receives the iteration count of the batch.  Returns
+ * DDTM_ERR_NOCONV if any right-hand side missed the tolerance. */
+int ddtm_coarse_solve_batch(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu_c, int loc, int* iters);
+
 /* ---- solve (Sec. 2.2, 2.5) ---------------------------------------------------- */
 
 /* Solve D(mu) x = b for nrhs right-hand sides to params.outer_tol (relative,

@@ -137,9 +137,13 @@ __global__ void k_galerkin(DS* __restrict__ Dc, const float2* __restrict__ P, Li
 // The same Galerkin products with the rows staged in shared memory, for FP16
 // coarse storage (the tensor-core images round D_c to FP16 anyway): one CTA
 // per (aggregate A, row chirality s) keeps the nv rows (s, i) of P on A as
-// FP16 in shared memory, computes for every column (s', j) the chirality-s
-// components of y_0 and of the face hops y_k as above, and projects them out
-// of shared memory, so P is not re-read from memory for every column.
+// FP16 in shared memory, computes for CC columns (s', j) at a time the
+// chirality-s components of y_0 and of the face hops y_k as above (each link
+// loaded once for the CC columns), and projects them out of shared memory, each
+// row entry loaded once for the CC columns, so P is not re-read from memory
+// for every column and the projections need fewer shared-memory loads per
+// multiply-add.  Every entry is the same sum, in the same order, for any CC.
+template <int CC>
 __global__ void __launch_bounds__(256, 1) k_galerkin_rows(float2* __restrict__ Dc, const float2* __restrict__ P,
                                                           Links<PREC_F32> U, Clover<PREC_F32> C, Geo g, FaceTables f,
                                                           int nv) {
@@ -149,69 +153,89 @@ __global__ void __launch_bounds__(256, 1) k_galerkin_rows(float2* __restrict__ D
   const int n = 2 * nv;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __half2* Ps = reinterpret_cast<__half2*>(smem_raw);                                // [nv][6][Vb]
-  cplx<float>* y0 = reinterpret_cast<cplx<float>*>(Ps + (size_t)nv * 6 * Vb);          // [6][Vb]
-  cplx<float>* yf = y0 + 6 * Vb;                                                       // [6][nf]
+  cplx<float>* y0 = reinterpret_cast<cplx<float>*>(Ps + (size_t)nv * 6 * Vb);          // [CC][6][Vb]
+  cplx<float>* yf = y0 + (size_t)CC * 6 * Vb;                                          // [CC][6][nf]
   const size_t rows0 = pix(A, s, 0, 0, 0, nv, Vb);
   for (int e = threadIdx.x; e < nv * 6 * Vb; e += blockDim.x) Ps[e] = __float22half2_rn(__ldg(P + rows0 + e));
-  for (int col = 0; col < n; col++) {
-    const int sp = col / nv, j = col - sp * nv;
+  for (int col0 = 0; col0 < n; col0 += CC) {
+    const int ncol = n - col0 < CC ? n - col0 : CC;
     for (int loc = threadIdx.x; loc < Vb; loc += blockDim.x) {
-      cplx<float> phi[12], acc[12], out[12];
+      cplx<float> acc[CC][12];
 #pragma unroll
-      for (int c = 0; c < 12; c++) {  // column (sp, j): chirality-sp components only (static indices)
-        phi[c] = (c / 6 == sp) ? ld(P + pix(A, sp, j, c % 6, loc, nv, Vb)) : cplx<float>(0, 0);
-        acc[c] = cplx<float>(0, 0);
-      }
-      C.apply(A, loc, phi, out);
+      for (int cc = 0; cc < CC; cc++)
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[cc][c] = cplx<float>(0, 0);
       for (int k = 0; k < 8; k++) {
         const int mu = k >> 1;
         const bool fwd = (k & 1) == 0;
         Nbr nb = neighbour(g, A, loc, k);
-        cplx<float> p[12], h[6], wv[6], u[9];
+        cplx<float> u[9];
+        if (fwd) U.load(A, loc, mu, u);
+        else U.load(nb.blk, nb.loc, mu, u);
+        const int slot = nb.cross ? f.off[k] + f.idx[k * Vb + loc] : 0;
 #pragma unroll
-        for (int c = 0; c < 12; c++)
-          p[c] = (c / 6 == sp) ? ld(P + pix(nb.blk, sp, j, c % 6, nb.loc, nv, Vb)) : cplx<float>(0, 0);
-        project<float>(mu, fwd, p, h);
-        if (fwd) { U.load(A, loc, mu, u); mul_U<float>(u, h, wv); }
-        else { U.load(nb.blk, nb.loc, mu, u); mul_Udag<float>(u, h, wv); }
-        if (nb.flip)
-          for (int q = 0; q < 6; q++) wv[q] = -wv[q];
-        if (!nb.cross) {
-          reconstruct<float>(mu, fwd, wv, acc);
-        } else {
-          cplx<float> part[12];
+        for (int cc = 0; cc < CC; cc++) {
+          if (cc >= ncol) break;
+          const int col = col0 + cc, sp = col / nv, j = col - sp * nv;
+          cplx<float> p[12], h[6], wv[6];
 #pragma unroll
-          for (int c = 0; c < 12; c++) part[c] = cplx<float>(0, 0);
-          reconstruct<float>(mu, fwd, wv, part);
-          const int slot = f.off[k] + f.idx[k * Vb + loc];
+          for (int c = 0; c < 12; c++)  // column (sp, j): chirality-sp components only (static indices)
+            p[c] = (c / 6 == sp) ? ld(P + pix(nb.blk, sp, j, c % 6, nb.loc, nv, Vb)) : cplx<float>(0, 0);
+          project<float>(mu, fwd, p, h);
+          if (fwd) mul_U<float>(u, h, wv);
+          else mul_Udag<float>(u, h, wv);
+          if (nb.flip)
+            for (int q = 0; q < 6; q++) wv[q] = -wv[q];
+          if (!nb.cross) {
+            reconstruct<float>(mu, fwd, wv, acc[cc]);
+          } else {
+            cplx<float> part[12];
 #pragma unroll
-          for (int c = 0; c < 6; c++) yf[c * nf + slot] = -0.5f * (s ? part[6 + c] : part[c]);
+            for (int c = 0; c < 12; c++) part[c] = cplx<float>(0, 0);
+            reconstruct<float>(mu, fwd, wv, part);
+#pragma unroll
+            for (int c = 0; c < 6; c++) yf[((size_t)cc * 6 + c) * nf + slot] = -0.5f * (s ? part[6 + c] : part[c]);
+          }
         }
       }
 #pragma unroll
-      for (int c = 0; c < 6; c++)
-        y0[c * Vb + loc] = s ? out[6 + c] + (-0.5f) * acc[6 + c] : out[c] + (-0.5f) * acc[c];
+      for (int cc = 0; cc < CC; cc++) {
+        if (cc >= ncol) break;
+        const int col = col0 + cc, sp = col / nv, j = col - sp * nv;
+        cplx<float> phi[12], out[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++)
+          phi[c] = (c / 6 == sp) ? ld(P + pix(A, sp, j, c % 6, loc, nv, Vb)) : cplx<float>(0, 0);
+        C.apply(A, loc, phi, out);
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+          y0[((size_t)cc * 6 + c) * Vb + loc] = s ? out[6 + c] + (-0.5f) * acc[cc][6 + c] : out[c] + (-0.5f) * acc[cc][c];
+      }
     }
     __syncthreads();
     const int GR = 4, ngr = (nv + GR - 1) / GR;
     for (int o = w; o < 9 * ngr; o += nw) {
       const int d = o / ngr, r0 = (o - d * ngr) * GR;
-      cplx<float> acc[GR];
+      cplx<float> acc[GR][CC];
       int ir[GR];
 #pragma unroll
       for (int r = 0; r < GR; r++) {
-        acc[r] = cplx<float>(0, 0);
+#pragma unroll
+        for (int cc = 0; cc < CC; cc++) acc[r][cc] = cplx<float>(0, 0);
         ir[r] = r0 + r < nv ? r0 + r : nv - 1;
       }
       if (d == 0) {
         for (int comp = 0; comp < 6; comp++)
 #pragma unroll 4
           for (int loc = lane; loc < Vb; loc += 32) {
-            const cplx<float> yv = y0[comp * Vb + loc];
+            cplx<float> yv[CC];
+#pragma unroll
+            for (int cc = 0; cc < CC; cc++) yv[cc] = y0[((size_t)cc * 6 + comp) * Vb + loc];
 #pragma unroll
             for (int r = 0; r < GR; r++) {
               const float2 pv = __half22float2(Ps[((size_t)ir[r] * 6 + comp) * Vb + loc]);
-              cmac_conj(acc[r], cplx<float>(pv.x, pv.y), yv);
+#pragma unroll
+              for (int cc = 0; cc < CC; cc++) cmac_conj(acc[r][cc], cplx<float>(pv.x, pv.y), yv[cc]);
             }
           }
       } else {
@@ -220,28 +244,33 @@ __global__ void __launch_bounds__(256, 1) k_galerkin_rows(float2* __restrict__ D
 #pragma unroll 2
           for (int q = f.off[k] + lane; q < f.off[k + 1]; q += 32) {
             const int fl = f.list[q];
-            const cplx<float> yv = yf[comp * nf + q];
+            cplx<float> yv[CC];
+#pragma unroll
+            for (int cc = 0; cc < CC; cc++) yv[cc] = yf[((size_t)cc * 6 + comp) * nf + q];
 #pragma unroll
             for (int r = 0; r < GR; r++) {
               const float2 pv = __half22float2(Ps[((size_t)ir[r] * 6 + comp) * Vb + fl]);
-              cmac_conj(acc[r], cplx<float>(pv.x, pv.y), yv);
+#pragma unroll
+              for (int cc = 0; cc < CC; cc++) cmac_conj(acc[r][cc], cplx<float>(pv.x, pv.y), yv[cc]);
             }
           }
       }
 #pragma unroll
-      for (int r = 0; r < GR; r++) {
-        acc[r].re = warp_sum(acc[r].re);
-        acc[r].im = warp_sum(acc[r].im);
-        if (lane == 0 && r0 + r < nv)
-          Dc[(((size_t)A * 9 + d) * n + col) * n + s * nv + r0 + r] = make_float2(acc[r].re, acc[r].im);
-      }
+      for (int r = 0; r < GR; r++)
+#pragma unroll
+        for (int cc = 0; cc < CC; cc++) {
+          acc[r][cc].re = warp_sum(acc[r][cc].re);
+          acc[r][cc].im = warp_sum(acc[r][cc].im);
+          if (lane == 0 && r0 + r < nv && cc < ncol)
+            Dc[(((size_t)A * 9 + d) * n + col0 + cc) * n + s * nv + r0 + r] = make_float2(acc[r][cc].re, acc[r][cc].im);
+        }
     }
     __syncthreads();
   }
 }
 
-static size_t galerkin_rows_smem(const FineGeom& g, const FaceDev& faces, int nv) {
-  return (size_t)nv * 6 * g.Vb * sizeof(__half2) + (size_t)6 * (g.Vb + faces.off[8]) * sizeof(cplx<float>);
+static size_t galerkin_rows_smem(const FineGeom& g, const FaceDev& faces, int nv, int cc) {
+  return (size_t)nv * 6 * g.Vb * sizeof(__half2) + (size_t)cc * 6 * (g.Vb + faces.off[8]) * sizeof(cplx<float>);
 }
 
 void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* Dc, const float2* P, const void* links32,
@@ -257,10 +286,13 @@ void launch_galerkin(const FineGeom& g, const FaceDev& faces, int dprec, void* D
   Links<PREC_F32> U{(const float2*)links32, g.Vb};
   Clover<PREC_F32> C{(const float2*)clover32, g.Vb};
   if (dprec != PREC_F32) throw Error(DDTM_ERR_ARG, "internal: Galerkin output is FP32");
-  const size_t srows = galerkin_rows_smem(g, faces, nv);
-  if (rows_fp16 && srows <= 220 * 1024) {
-    set_dynamic_smem((const void*)k_galerkin_rows, srows);
-    k_galerkin_rows<<<g.Nb * 2, threads, srows, st>>>((float2*)Dc, P, U, C, q, f, nv);
+  const size_t srows1 = galerkin_rows_smem(g, faces, nv, 1), srows2 = galerkin_rows_smem(g, faces, nv, 2);
+  if (rows_fp16 && srows2 <= 224 * 1024) {  // two columns per pass where the shared memory holds them
+    set_dynamic_smem((const void*)k_galerkin_rows<2>, srows2);
+    k_galerkin_rows<2><<<g.Nb * 2, threads, srows2, st>>>((float2*)Dc, P, U, C, q, f, nv);
+  } else if (rows_fp16 && srows1 <= 220 * 1024) {
+    set_dynamic_smem((const void*)k_galerkin_rows<1>, srows1);
+    k_galerkin_rows<1><<<g.Nb * 2, threads, srows1, st>>>((float2*)Dc, P, U, C, q, f, nv);
   } else {
     set_dynamic_smem((const void*)k_galerkin<float2>, smem);
     k_galerkin<float2><<<g.Nb, threads, smem, st>>>((float2*)Dc, P, U, C, q, f, nv);

@@ -55,14 +55,16 @@ struct TcGeom {
 };
 TcGeom tc_geom(int n, int R);
 bool tc_supported(int n);
-// Dct: matrix images of the 9 blocks of every site (from Dc); Dinvt: of Dinv
+// Dct: matrix images of the 9 blocks of every site (from Dc)
 void build_coarse_images(CoarseLevel& c, cudaStream_t st);
+// Dhopt: images of D_ee^-1(e) A_d(e) for the 8 hop blocks of every even site e (from Dinv and Dc), so
+// that one pass forms D_ee^-1 D_eo x of the even-odd reduced operator
 void build_inverse_images(CoarseLevel& c, cudaStream_t st);
 size_t tc_vector_image_bytes(const CoarseLevel& c, int nsites, int R);
 // x: interleaved batch of type tag x_type (1 FP32, 2 FP16)
 void launch_vector_image(const CoarseLevel& c, void* img, const void* x, int x_type, int nsites, int R, cudaStream_t st);
 // One stencil pass over output slots idx < nout:
-//   acc = [self] A_self(idx) X_self(idx) + [hops] sum_d A_d(site) X_hop(tab[d-1][idx])
+//   acc = [self] A_self(idx) X_self(idx) + [hops] sum_d A_d(site or idx) X_hop(tab[d-1][idx])
 //   y  = sy * yin + sres * (acc + i mu_c Gamma5_c xs)   (FP32, if y)
 //   yt = FP16 vector image of the same value            (if yt)
 struct TcPass {
@@ -72,6 +74,7 @@ struct TcPass {
   size_t a_self_stride = 0;
   bool self_by_site = false;  // A_self indexed by osite[idx] (else by idx)
   const void* A_hop = nullptr;
+  bool hop_by_slot = false;   // hop d of slot idx at A_hop + (idx * 8 + d - 1) (else (site * 9 + d)) blocks
   const void* X_self = nullptr;
   const void* X_hop = nullptr;
   const int* tab = nullptr;

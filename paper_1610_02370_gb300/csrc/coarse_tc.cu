@@ -140,7 +140,8 @@ struct TcArgs {
   const char* A_self;   // self item of output slot idx: A_self + key * a_self_stride, key = osite[idx] or idx
   size_t a_self_stride;
   int self_by_site;
-  const char* A_hop;    // hop item d = 1..8 of site s: A_hop + (s * 9 + d) * a_bytes
+  const char* A_hop;    // hop item d = 1..8 of site s: A_hop + (s * 9 + d) * a_bytes (hop_by_slot: (idx * 8 + d - 1))
+  int hop_by_slot;
   const char* X_self;   // vector image of the self item: X_self + idx * b_bytes
   const char* X_hop;    // hop item d: X_hop + tab[(d - 1) * nout + idx] * b_bytes
   const int* tab;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(192, tc_ctas_per_sm(NGJ)) k_coarse_tc(const Tc
             Xg = a.X_self + (size_t)idx * a.b_bytes + xoff;
           } else {
             const int d = t - a.self + 1;
-            Ag = a.A_hop + ((size_t)site * 9 + d) * a.a_bytes;
+            Ag = a.A_hop + (a.hop_by_slot ? (size_t)idx * 8 + (d - 1) : (size_t)site * 9 + d) * a.a_bytes;
             Xg = a.X_hop + (size_t)src[d - 1] * a.b_bytes + xoff;
           }
           ptx::mbar_arrive_expect_tx(FULL + 8u * s, stage_tx);
@@ -416,11 +417,61 @@ void build_coarse_images(CoarseLevel& c, cudaStream_t st) {
   CK(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), st));
 }
 
+
+// Images of B = Dinv(e) A_d(e), d = 1..8, for every even site e: thread (block, row pair i, column group
+// h) forms B[i][8h .. 8h+7] (FP32 sums over k in order) and writes image rows 2i (real parts) and 2i + 1
+// (imaginary parts); rows and columns beyond n are the zero padding.  Both factors are column-major
+// n x n blocks.
+__global__ void k_hop_inverse_image(char* __restrict__ img, const float2* __restrict__ Dinv,
+                                    const float2* __restrict__ Dc, const int* __restrict__ even, int ne, int n,
+                                    int arows, int kpad, int sbo, int a_bytes) {
+  const int kg = kpad / 8, hrows = arows / 2;
+  const size_t per = (size_t)hrows * kg;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (size_t)ne * 8 * per) return;
+  const size_t b = tid / per;  // block e * 8 + (d - 1)
+  const int rem = (int)(tid - b * per), i = rem % hrows, h = rem / hrows;
+  const int e = (int)(b / 8), d = (int)(b % 8) + 1;
+  const float2* Di = Dinv + (size_t)e * n * n;                       // column k at Di + k n
+  const float2* Ad = Dc + ((size_t)__ldg(even + e) * 9 + d) * n * n;  // column j at Ad + j n
+  float re[8], im[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) re[q] = im[q] = 0.f;
+  if (i < n) {
+    for (int k = 0; k < n; k++) {
+      const float2 a = __ldg(Di + (size_t)k * n + i);
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int j = 8 * h + q;
+        if (j < n) {
+          const float2 bkj = __ldg(Ad + (size_t)j * n + k);
+          re[q] += a.x * bkj.x - a.y * bkj.y;
+          im[q] += a.x * bkj.y + a.y * bkj.x;
+        }
+      }
+    }
+  }
+  __align__(16) __half vr[8], vi[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    vr[q] = __float2half_rn(re[q]);
+    vi[q] = __float2half_rn(im[q]);
+  }
+  char* base = img + b * a_bytes;
+  *reinterpret_cast<uint4*>(base + img_off(2 * i, 8 * h, sbo)) = *reinterpret_cast<const uint4*>(vr);
+  *reinterpret_cast<uint4*>(base + img_off(2 * i + 1, 8 * h, sbo)) = *reinterpret_cast<const uint4*>(vi);
+}
+
 void build_inverse_images(CoarseLevel& c, cudaStream_t st) {
   TcGeom t = tc_geom(c.n, 1);
-  size_t ne = c.h_even.size();
-  c.Dinvt.ensure(ne * t.a_bytes);
-  matrix_images(c, c.Dinvt.as<char>(), c.Dinv.as<float2>(), ne, st);
+  const size_t ne = c.h_even.size();
+  c.Dhopt.ensure(ne * 8 * t.a_bytes);
+  const size_t tot = ne * 8 * (size_t)(t.arows / 2) * (t.kpad / 8);
+  if (!tot) return;
+  k_hop_inverse_image<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c.Dhopt.as<char>(), c.Dinv.as<float2>(),
+                                                                     c.Dc.as<float2>(), c.even.as<int>(), (int)ne,
+                                                                     c.n, t.arows, t.kpad, t.sbo, t.a_bytes);
+  CKL("hop_inverse_image");
 }
 
 // ---- autotuner ---------------------------------------------------------------------------------
@@ -538,6 +589,7 @@ static void launch_coarse_tc_cps(const CoarseLevel& c, const TcPass& p, int R, c
     a.a_self_stride = p.a_self_stride;
     a.self_by_site = p.self_by_site;
     a.A_hop = (const char*)p.A_hop;
+    a.hop_by_slot = p.hop_by_slot ? 1 : 0;
     a.X_self = (const char*)p.X_self;
     a.X_hop = (const char*)p.X_hop;
     a.tab = p.tab;

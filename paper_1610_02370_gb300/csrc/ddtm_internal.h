@@ -86,7 +86,8 @@ struct CoarseLevel {
   int prec = 1;                // F32: SIMT stencil; F16: tensor-core stencil on FP16 images
   DevBuf Dc;                   // [site][9][col][row] complex FP32, see coarse.cu
   DevBuf Dinv;                 // inverses of (self + i mu_c Gamma5_c) on even sites, FP32
-  DevBuf Dct, Dinvt;           // FP16 matrix images of Dc and Dinv (prec F16), see coarse_tc.cu
+  DevBuf Dct;                  // FP16 matrix images of Dc (prec F16), see coarse_tc.cu
+  DevBuf Dhopt;                // FP16 images of Dinv(e) A_d(e), the 8 hops of every even site (prec F16)
   DevBuf tc_err;               // set by a tensor-core pass that gave up waiting
   double inv_mu = 0;
   bool inv_valid = false;

@@ -425,31 +425,22 @@ int coarse_eo_solve(ddtm_ctx* c, cplx<float>* x_full, const cplx<float>* b_full,
     // only the input and the output of D_hat are FP32 vectors
     const size_t img_o = tc_vector_image_bytes(L, (int)no, Rc), img_e = tc_vector_image_bytes(L, (int)ne, Rc);
     char* vt = (char*)c->scratch.get("ceo_vt", img_o);
-    char* ht = (char*)c->scratch.get("ceo_ht", img_e);
     char* tt = (char*)c->scratch.get("ceo_tt", img_e);
     const size_t ab = tc_geom(L.n, 1).a_bytes;
-    Dhat = [&, vt, ht, tt, ab](cplx<float>* out, const void* in, int in_type) {
+    Dhat = [&, vt, tt, ab](cplx<float>* out, const void* in, int in_type) {
       launch_vector_image(L, vt, in, in_type, (int)no, Rc, c->stream);
-      TcPass h;  // ht = D_eo in
+      TcPass h;  // tt = -D_ee^-1 D_eo in, from the products D_ee^-1(e) A_d(e) (one pass, no intermediate)
       h.name = "coarse_tc_hop_even";
       h.hops = true;
-      h.A_hop = L.Dct.p;
+      h.A_hop = L.Dhopt.p;
+      h.hop_by_slot = true;
       h.X_hop = vt;
       h.tab = L.nbr_eo.as<int>();
       h.osite = L.even.as<int>();
       h.nout = (int)ne;
-      h.yt = ht;
+      h.sres = -1.f;
+      h.yt = tt;
       launch_coarse_tc(L, h, Rc, c->stream);
-      TcPass v;  // tt = -D_ee^-1 ht
-      v.name = "coarse_tc_inverse";
-      v.self = true;
-      v.A_self = L.Dinvt.p;
-      v.a_self_stride = ab;
-      v.X_self = ht;
-      v.nout = (int)ne;
-      v.sres = -1.f;
-      v.yt = tt;
-      launch_coarse_tc(L, v, Rc, c->stream);
       TcPass o;  // out = (D_oo + i mu_c Gamma5_c) in + D_oe tt
       o.name = "coarse_tc_odd";
       o.self = o.hops = true;
@@ -1122,6 +1113,43 @@ int ddtm_prolong(ddtm_ctx* ctx, int level, double* x, const double* cin, int nrh
     }
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  API_END(ctx)
+}
+
+int ddtm_coarse_solve_batch(ddtm_ctx* ctx, double* x, const double* b, int nrhs, double mu_c, int loc, int* iters) {
+  API_BEGIN(ctx)
+  check_loc(loc);
+  if (!x || !b || nrhs < 0 || !std::isfinite(mu_c)) throw Error(DDTM_ERR_ARG, "invalid arguments");
+  require_hierarchy(ctx);
+  if (iters) *iters = 0;
+  if (nrhs == 0) return DDTM_OK;
+  CoarseLevel& L = coarsest(ctx);
+  const size_t nc = (size_t)L.Nc * L.n;
+  const int Rc = coarse_batch(nrhs);  // the batch the solver's kernels take, padded with zero columns
+  cplx<float>* bv = (cplx<float>*)ctx->scratch.get("abi_cb", nc * Rc * 8);
+  cplx<float>* xv = (cplx<float>*)ctx->scratch.get("abi_cx", nc * Rc * 8);
+  CK(cudaMemsetAsync(bv, 0, nc * Rc * 8, ctx->stream));
+  for (int r = 0; r < nrhs; r++) {
+    const double* din = stage_in(ctx, "canon_cin", b + 2 * nc * r, nc, loc);
+    launch_coarse_interleave(L, bv, const_cast<double*>(din), r, Rc, 0, ctx->stream);
+  }
+  std::vector<double> rr(Rc, 0.0);
+  const int it = coarse_eo_solve(ctx, xv, bv, Rc, mu_c, ctx->p.coarse_restart, ctx->p.coarse_max_restarts,
+                                 ctx->p.coarse_tol, rr.data());
+  for (int r = 0; r < nrhs; r++) {
+    double* dout = stage_out(ctx, "canon_cout", x + 2 * nc * r, nc, loc);
+    launch_coarse_interleave(L, xv, dout, r, Rc, 1, ctx->stream);
+    unstage_out(ctx, x + 2 * nc * r, dout, nc, loc);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  check_tc_error(L);
+  if (iters) *iters = it;
+  double worst = 0;
+  for (int r = 0; r < nrhs; r++) worst = rr[r] > worst ? rr[r] : worst;
+  if (worst > ctx->p.coarse_tol) {
+    ctx->err = "coarse solve stopped at relative residual " + std::to_string(worst);
+    return DDTM_ERR_NOCONV;
+  }
   API_END(ctx)
 }
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "ddtm_prolong": (_I, [_P, _I, _P, _P, _I, _I]),
     "ddtm_apply_Dc": (_I, [_P, _I, _P, _P, _I, _D, _I]),
     "ddtm_coarse_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I)]),
+    "ddtm_coarse_solve_batch": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I)]),
     "ddtm_sap_coarse": (_I, [_P, _I, _P, _P, _I, _D, _I, _I, _I]),
     "ddtm_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(ddtm_solve_info)]),
     "ddtm_eo_cg": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, ctypes.POINTER(ddtm_solve_info)]),
@@ -276,6 +277,15 @@ def ddtm_coarse_solve(ctx, x, b, mu_c):
     bxx, bb = _buf(x, True), _buf(b)
     it = _I(0)
     code = _lib.ddtm_coarse_solve(ctx, bxx[0], bb[0], mu_c, _same_loc(bxx, bb), ctypes.byref(it))
+    if code not in (OK, ERR_NOCONV):
+        _check(ctx, code)
+    return it.value, code
+
+
+def ddtm_coarse_solve_batch(ctx, x, b, nrhs, mu_c):
+    bxx, bb = _buf(x, True), _buf(b)
+    it = _I(0)
+    code = _lib.ddtm_coarse_solve_batch(ctx, bxx[0], bb[0], nrhs, mu_c, _same_loc(bxx, bb), ctypes.byref(it))
     if code not in (OK, ERR_NOCONV):
         _check(ctx, code)
     return it.value, code

@@ -5,13 +5,15 @@ for timing and for profiling a single kernel in isolation.
     python -m paper_1610_02370_gb300.kernel_bench dslash --dims 64 32 32 32 --prec 1 --nrhs 1 --reps 10
     python -m paper_1610_02370_gb300.kernel_bench solve --dims 64 32 32 32 --nrhs 12 --outer-iters 1
     python -m paper_1610_02370_gb300.kernel_bench sap --dims 48 24 24 24 --nrhs 12 --cycles 2
+    python -m paper_1610_02370_gb300.kernel_bench csolve --dims 64 32 32 32 --nrhs 12 --ctol 1e-2
 
 ``coarse`` builds the aggregation and the Galerkin coarse operator from
 Gaussian test vectors (no setup iterations; the second build is timed per
 kernel) and applies the coarse operator D_c (Sec. 2.3) to a batch of nrhs
 vectors; ``dslash`` applies D(mu) (Sec. 2.1) to one field; ``solve`` runs the
 first outer iterations of a batched solve (every kernel of the solve phase);
-``sap`` runs the SAP smoother (Sec. 2.4) on a batch of Gaussian right-hand sides.
+``sap`` runs the SAP smoother (Sec. 2.4) on a batch of Gaussian right-hand sides;
+``csolve`` runs the batched coarsest-level GMRES (Sec. 2.5).
 Each prints one JSON line with its times (CUDA events).
 """
 
@@ -104,6 +106,37 @@ def solve(args):
         ddtm.ddtm_destroy(ctx)
 
 
+def csolve(args):
+    """Batched coarsest-level even-odd GMRES (Sec. 2.5) on nrhs Gaussian coarse
+    vectors after an aggregation from Gaussian test vectors: the tensor-core
+    Schur complement and the FP16-basis Gram-Schmidt kernels at the sizes of
+    the solver's coarse solves (restart 100, tolerance --ctol)."""
+    dims = tuple(args.dims)
+    U = synth.gauge_field(dims, args.eps, seed=0, device="cuda")
+    ctx = ddtm.ddtm_create(dims, (4, 4, 4, 4), 0)
+    try:
+        ddtm.ddtm_load_gauge(ctx, U, args.kappa, args.csw)
+        del U
+        p = ddtm.ddtm_get_params(ctx)
+        p.nv[0] = args.nv
+        p.coarse_prec = args.coarse_prec
+        p.coarse_tol = args.ctol
+        ddtm.ddtm_set_params(ctx, p)
+        v = synth.gaussian_vectors((args.nv,) + tuple(dims) + (4, 3), seed=5, device="cuda")
+        ddtm.ddtm_set_test_vectors(ctx, 0, v, args.nv)
+        del v
+        torch.cuda.empty_cache()
+        cl = tuple(d // 4 for d in dims)
+        b = synth.gaussian_vectors((args.nrhs,) + cl + (2 * args.nv,), seed=6, device="cuda")
+        x = torch.zeros_like(b)
+        res = {}
+        ms = _events(lambda: res.update(out=ddtm.ddtm_coarse_solve_batch(ctx, x, b, args.nrhs, args.muc)), args.reps)
+        print(json.dumps({"kernel": "csolve", "dims": dims, "nv": args.nv, "nrhs": args.nrhs, "ctol": args.ctol,
+                          "iters": res["out"][0], "code": res["out"][1], "ms_per_call": ms}))
+    finally:
+        ddtm.ddtm_destroy(ctx)
+
+
 def sap(args):
     """SAP smoother (Sec. 2.4) on a batch of nrhs Gaussian right-hand sides from x = 0."""
     dims = tuple(args.dims)
@@ -148,7 +181,7 @@ def dslash(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["coarse", "dslash", "solve", "sap"])
+    ap.add_argument("what", choices=["coarse", "dslash", "solve", "sap", "csolve"])
     ap.add_argument("--dims", type=int, nargs=4, default=[48, 24, 24, 24])
     ap.add_argument("--eps", type=float, default=0.15)
     ap.add_argument("--kappa", type=float, default=0.137)
@@ -163,10 +196,12 @@ def main():
     ap.add_argument("--sap-prec", type=int, default=2)
     ap.add_argument("--cycles", type=int, default=2)
     ap.add_argument("--nmr", type=int, default=3)
+    ap.add_argument("--ctol", type=float, default=1e-2)
+    ap.add_argument("--muc", type=float, default=0.0078)
     args = ap.parse_args()
     from . import build
     build.build()
-    {"coarse": coarse, "dslash": dslash, "solve": solve, "sap": sap}[args.what](args)
+    {"coarse": coarse, "dslash": dslash, "solve": solve, "sap": sap, "csolve": csolve}[args.what](args)
 
 
 if __name__ == "__main__":

@@ -121,6 +121,28 @@ def test_tc_coarse_eo_solve(lib, eo_case):
     assert np.linalg.norm(r[par == 0]) < 1e-4 * np.linalg.norm(b.numpy())
 
 
+@pytest.mark.parametrize("nrhs", [5, 12])
+def test_tc_coarse_eo_solve_batch(lib, eo_case, nrhs):
+    """The batched coarsest solve (5 right-hand sides padded to 8, and 12):
+    every rhs reaches the FP16 operator accuracy against the oracle's D_c."""
+    c = eo_case
+    cl = c.cop.lat
+    muc = 0.5
+    b = synth.gaussian_vectors((nrhs,) + cl + (2 * c.nv,), seed=16)
+    p = lib.ddtm_get_params(c.ctx)
+    p.coarse_tol = 1e-5
+    p.coarse_restart = 60
+    lib.ddtm_set_params(c.ctx, p)
+    lib.ddtm_set_test_vectors(c.ctx, 0, c.v.cuda(), c.nv)
+    x = torch.zeros_like(b).cuda()
+    it, code = lib.ddtm_coarse_solve_batch(c.ctx, x, b.cuda(), nrhs, muc)
+    assert code == lib.OK and it > 0
+    xh = x.cpu().numpy()
+    for r in range(nrhs):
+        res = b[r].numpy() - c.cop.apply(xh[r], muc)
+        assert np.linalg.norm(res) < 3e-3 * np.linalg.norm(b[r].numpy()), r
+
+
 def test_tc_two_level_solve_12rhs(lib):
     """12 right-hand sides through the two-level solve with the tensor-core coarse
     stencil: every system reaches FP64 relative residual 1e-10 (oracle's D), in
