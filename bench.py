@@ -107,7 +107,7 @@ def algorithmic_bytes(name, V, Vb, b, nv, Nc, rhs=1.0):
 # DRAM traffic per unit from one ncu capture of the kernel as it stands (profiles/), scaled to a
 # launch of the bench workload by the units it processes; remove an entry when its kernel changes.
 NCU_TRAFFIC = {
-    "sap_half_f16": {"bytes_per_site_rhs": 1.0754e9 / (663552 / 2 * 12), "capture": "k_sap_half_24x24x24x48.md"},
+    "sap_half_f16": {"bytes_per_site_rhs": 1.0728e9 / (663552 / 2 * 12), "capture": "k_sap_half_24x24x24x48.md"},
 }
 
 
