@@ -661,7 +661,9 @@ def main():
     counts = ddtm.ddtm_timer_report(ctx)
     instrumented_ms = ei0.elapsed_time(ei1)
 
-    # residual of the timed solutions with the library's FP64 operator
+    # residual of the timed solutions with the library's FP64 operator (the solver's workspace is
+    # released first: on the largest lattices it holds most of the device memory)
+    ddtm.ddtm_release_workspace(ctx)
     r = torch.empty_like(x)
     ddtm.ddtm_apply_D(ctx, r, x_timed, NRHS, twists[-1] * mu, ddtm.PREC_F64)
     r = b - r

@@ -335,6 +335,12 @@ int ddtm_autotune_report(char* buf, int len);
  * caller that shares the GPU keep the solver within a share of HBM (the paper
  * has no counterpart; it runs one solver per node). */
 int ddtm_set_memory_limit(size_t bytes);
+
+/* Frees the context's solver workspace (Krylov bases, batched fields, staging
+ * buffers; the cached graphs that refer to them are destroyed) after
+ * synchronising its stream.  The gauge field, the hierarchy and the setup
+ * stay; the next call that needs workspace allocates it again. */
+int ddtm_release_workspace(ddtm_ctx* ctx);
 /* Device bytes the library holds now (all contexts and fields). */
 int ddtm_memory_in_use(size_t* bytes);
 

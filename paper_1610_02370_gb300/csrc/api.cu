@@ -418,6 +418,16 @@ int ddtm_autotune_report(char* buf, int len) {
   return DDTM_OK;
 }
 
+int ddtm_release_workspace(ddtm_ctx* ctx) {
+  API_BEGIN(ctx)
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& kv : ctx->graphs)  // captured graphs refer to the workspace
+    if (kv.second.first) CK(cudaGraphExecDestroy(kv.second.first));
+  ctx->graphs.clear();
+  ctx->scratch.clear();
+  API_END(ctx)
+}
+
 int ddtm_set_memory_limit(size_t bytes) {
   set_device_memory_limit(bytes);
   return DDTM_OK;

@@ -140,6 +140,7 @@ struct ScratchPool {
   std::map<std::string, DevBuf*> bufs;
   ~ScratchPool();
   void* get(const std::string& name, size_t bytes);
+  void clear();                                       // frees every buffer
   size_t held(const std::string& prefix) const;  // bytes held by buffers whose name starts with prefix
 };
 

@@ -85,8 +85,11 @@ void DevBuf::ensure(size_t n) {
   g_alloc_gen.fetch_add(1);
 }
 
-ScratchPool::~ScratchPool() {
+ScratchPool::~ScratchPool() { clear(); }
+
+void ScratchPool::clear() {
   for (auto& kv : bufs) delete kv.second;
+  bufs.clear();
 }
 
 void* ScratchPool::get(const std::string& name, size_t bytes) {

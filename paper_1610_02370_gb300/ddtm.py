@@ -86,6 +86,7 @@ SIGNATURES = {
     "ddtm_timer_report": (_I, [_P, ctypes.c_char_p, _I]),
     "ddtm_measure_fma_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ddtm_set_memory_limit": (_I, [ctypes.c_size_t]),
+    "ddtm_release_workspace": (_I, [_P]),
     "ddtm_set_option": (_I, [_P, ctypes.c_char_p, _I]),
     "ddtm_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_I)]),
     "ddtm_autotune_report": (_I, [ctypes.c_char_p, _I]),
@@ -361,6 +362,10 @@ def ddtm_memory_in_use():
     n = ctypes.c_size_t(0)
     _check(None, _lib.ddtm_memory_in_use(ctypes.byref(n)))
     return n.value
+
+
+def ddtm_release_workspace(ctx):
+    _check(ctx, _lib.ddtm_release_workspace(ctx))
 
 
 def ddtm_set_option(ctx, name, value):

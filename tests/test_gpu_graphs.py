@@ -47,6 +47,15 @@ def test_graph_replay_is_bit_identical(lib, coarse_prec):
             x1, n1, c1 = out[(1, rep)]
             assert torch.equal(x0, x1), rep
             assert (n1, c1) == (n0, c0), rep
+        # releasing the workspace frees the library's buffers and drops the cached graphs; the next
+        # solve allocates again and gives the same bits
+        before = lib.ddtm_memory_in_use()
+        lib.ddtm_release_workspace(ctx)
+        assert lib.ddtm_get_option(ctx, "graphs_cached") == 0
+        assert lib.ddtm_memory_in_use() < before
+        x = torch.zeros_like(b)
+        info, code = lib.ddtm_solve(ctx, x, b, 4, mu)
+        assert code == lib.OK and torch.equal(x, x0)
     finally:
         lib.ddtm_destroy(ctx)
 
