@@ -15,11 +15,18 @@
 #include "ddtm_internal.h"
 #include "timer.h"
 
+// Launch shapes of the coarse Gram-Schmidt kernels, measured on the 32^3 x 64 propagator step (one
+// wave of resident CTAs in every case): multi-dot over groups of DOTS_JB basis vectors with spans of
+// DOTS_EPT pairs per thread (JB 4: 523 ms, 2: 540, 8: 812, 16: 2623 per step; EPT 2 and 8 slower), and
+// multi-axpy with MAXPY_UNROLL basis vectors in flight (2: 675 ms, 1: 840, 4: 806, 8: 892).
 #ifndef DDTM_DOTS_EPT
 #define DDTM_DOTS_EPT 4
 #endif
+#ifndef DDTM_DOTS_JB
+#define DDTM_DOTS_JB 4
+#endif
 #ifndef DDTM_MAXPY_UNROLL
-#define DDTM_MAXPY_UNROLL 4
+#define DDTM_MAXPY_UNROLL 2
 #endif
 
 namespace ddtm {
@@ -548,7 +555,7 @@ static double set_bytes(const VSet& v) {
 static const char* fam(const VSet& w, const char* coarse, const char* fine) { return w.inter ? coarse : fine; }
 
 // basis vectors per multi-dot CTA; pairs per thread and span of the multi-dot
-static const int DOTS_JB = 8, DOTS_EPT = DDTM_DOTS_EPT;
+static const int DOTS_JB = DDTM_DOTS_JB, DOTS_EPT = DDTM_DOTS_EPT;
 
 // CTAs of a kernel the GPU holds at once for a block size and dynamic shared
 // memory (cached per kernel and shape).
