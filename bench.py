@@ -154,9 +154,10 @@ def parse_args():
     ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the oracle residual of the full-size solutions")
-    ap.add_argument("--study", choices=["eo-cg", "aggregation", "levels"], default=None,
+    ap.add_argument("--study", choices=["eo-cg", "aggregation", "levels", "oracle"], default=None,
                     help="eo-cg: the even-odd CG baseline against DD-alpha-AMG, t_total = t_setup + n_rhs t_solve "
                          "(Sec. 3.1.2, Fig. 3); aggregation: block size x N_v sweep (Sec. 3.3, Table 4)")
+    ap.add_argument("--lattices", default=None, help="--study oracle: comma-separated lattices (default: all four)")
     ap.add_argument("--oracle-units", default=None, help=argparse.SUPPRESS)  # child process of the CPU baseline
     return ap.parse_args()
 
@@ -265,6 +266,51 @@ def oracle_unit_times(wl, sample_dims=(16, 8, 8, 8)):
     out["coarse_iter"] = t / nit / Nc
     out["_sample"] = "x".join(str(d) for d in (sample_dims[1], sample_dims[2], sample_dims[3], sample_dims[0]))
     return out
+
+
+def oracle_study(only=None):
+    """The oracle as it stands, timed directly (no extrapolation) on this host in one process: at
+    the four lattices of the parameter sets (4^4 with 2^4 blocks; 16^3x32, 24^3x48 and 32^3x64 with
+    4^4 blocks) the construction of the operator (clover term), one application of D(mu) and one SAP
+    cycle (red and black half-sweeps, Sec. 2.4) on one Gaussian right-hand side, and on 4^4 the
+    plain FP64 GMRES solve to relative residual 1e-10.  Run it with one BLAS / OpenMP thread for a
+    single-core figure."""
+    import numpy as np
+    from oracle import krylov, sap
+    from oracle.operators import FineOperator
+    from paper_1610_02370_gb300 import synth
+
+    cases = [("4x4x4x4", (4, 4, 4, 4), 0.3, 0.125, 1.0, 0.01, (2, 2, 2, 2), 4)]
+    for name, nmr in (("16x16x16x32", 4), ("24x24x24x48", MG["nmr"]), ("32x32x32x64", MG["nmr"])):
+        w = WORKLOADS[name]
+        cases.append((name, w["dims"], w["eps"], w["kappa"], w["c_sw"], w["mu"], MG["block"], nmr))
+    rows = []
+    for name, dims, eps, kappa, csw, mu, blk, nmr in cases:
+        if only and name not in only:
+            continue
+        t0 = time.perf_counter()
+        op = FineOperator(synth.gauge_field(dims, eps, seed=0).numpy(), kappa, csw)
+        t_build = time.perf_counter() - t0
+        b = synth.gaussian_spinor(dims, seed=1).numpy()
+        t0 = time.perf_counter()
+        op.apply(b, mu)
+        t_d = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sap.sap(op, b, mu, blk, 1, nmr, eo=True)
+        t_sap = time.perf_counter() - t0
+        row = {"lattice": name, "sites": int(np.prod(dims)), "operator_build_s": t_build, "apply_D_s": t_d,
+               "sap_cycle_s": t_sap, "sap_blocks": list(blk), "nmr": nmr}
+        if name == "4x4x4x4":
+            t0 = time.perf_counter()
+            _, info = krylov.gmres(lambda v: op.apply(v, mu), b, 30, 100, 1e-10)
+            row.update(gmres_solve_s=time.perf_counter() - t0, gmres_relres=float(info["relres"]),
+                       gmres_iters=int(info.get("iters", 0)))
+        rows.append(row)
+        sys.stderr.write("[oracle] %s\n" % json.dumps(row))
+        sys.stderr.flush()
+        del op
+    print(json.dumps({"study": "oracle", "host": host_cpu(), "threads": os.environ.get("OMP_NUM_THREADS"),
+                      "rows": rows}))
 
 
 def host_cpu():
@@ -542,6 +588,9 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.study == "oracle":
+        oracle_study(args.lattices.split(",") if args.lattices else None)
         return
     if args.study:
         study(args)

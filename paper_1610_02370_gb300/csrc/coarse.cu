@@ -513,12 +513,13 @@ __global__ void k_coarse_interleave(float2* __restrict__ v, double* __restrict__
 }
 
 // Inverse of (self block + i mu_c Gamma5_c) per even site by Gauss-Jordan
-// elimination with partial pivoting in FP64; one CTA per site, thread = row.
-template <typename DS>
+// elimination with partial pivoting in CT (FP64, or FP32 where the inverses
+// only feed FP16 operator images); one CTA per site, thread = row.
+template <typename DS, typename CT>
 __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__ Dc, const int* __restrict__ even, int n,
                                int nv, double mu_c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<double>* M = reinterpret_cast<cplx<double>*>(smem_raw);  // [n][2n] row-major augmented
+  cplx<CT>* M = reinterpret_cast<cplx<CT>*>(smem_raw);  // [n][2n] row-major augmented
   __shared__ int piv;
   const int e = blockIdx.x, site = even[e];
   const int r = threadIdx.x;
@@ -526,16 +527,16 @@ __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__
   if (r < n) {
     for (int c = 0; c < n; c++) {
       cplx<float> a = ldD<DS>(Dc + ((size_t)site * 9 * n + c) * n + r);  // d = 0, column c, row r
-      M[r * w2 + c] = cplx<double>(a.re, a.im);
-      M[r * w2 + n + c] = cplx<double>(r == c ? 1.0 : 0.0, 0.0);
+      M[r * w2 + c] = cplx<CT>((CT)a.re, (CT)a.im);
+      M[r * w2 + n + c] = cplx<CT>(r == c ? CT(1) : CT(0), CT(0));
     }
-    M[r * w2 + r].im += r < nv ? mu_c : -mu_c;
+    M[r * w2 + r].im += (CT)(r < nv ? mu_c : -mu_c);
   }
   __syncthreads();
   for (int c = 0; c < n; c++) {
     if (r == 0) {
       int p = c;
-      double best = norm2(M[c * w2 + c]);
+      CT best = norm2(M[c * w2 + c]);
       for (int k = c + 1; k < n; k++)
         if (norm2(M[k * w2 + c]) > best) { best = norm2(M[k * w2 + c]); p = k; }
       piv = p;
@@ -544,27 +545,27 @@ __global__ void k_self_inverse(float2* __restrict__ Dinv, const DS* __restrict__
     const int p = piv;
     if (p != c && r < w2) {  // swap rows c and p, column r (and r + n) per thread
       for (int cc = r; cc < w2; cc += blockDim.x) {
-        cplx<double> tmp = M[c * w2 + cc];
+        cplx<CT> tmp = M[c * w2 + cc];
         M[c * w2 + cc] = M[p * w2 + cc];
         M[p * w2 + cc] = tmp;
       }
     }
     __syncthreads();
-    cplx<double> d = M[c * w2 + c];
-    double dn = norm2(d);
-    cplx<double> inv(d.re / dn, -d.im / dn);
+    cplx<CT> d = M[c * w2 + c];
+    CT dn = norm2(d);
+    cplx<CT> inv(d.re / dn, -d.im / dn);
     __syncthreads();
     for (int cc = r; cc < w2; cc += blockDim.x) M[c * w2 + cc] = M[c * w2 + cc] * inv;
     __syncthreads();
     if (r < n && r != c) {
-      cplx<double> fct = M[r * w2 + c];
+      cplx<CT> fct = M[r * w2 + c];
       for (int cc = 0; cc < w2; cc++) M[r * w2 + cc] = M[r * w2 + cc] - fct * M[c * w2 + cc];
     }
     __syncthreads();
   }
   if (r < n)
     for (int c = 0; c < n; c++) {
-      cplx<double> v = M[r * w2 + n + c];
+      cplx<CT> v = M[r * w2 + n + c];
       Dinv[((size_t)e * n + c) * n + r] = make_float2((float)v.re, (float)v.im);  // column-major
     }
 }
@@ -655,8 +656,17 @@ void launch_self_inverse(CoarseLevel& c, double mu_c, cudaStream_t st) {
   c.Dinv.ensure((size_t)ne * c.n * c.n * sizeof(float2));
   size_t smem = (size_t)c.n * 2 * c.n * sizeof(cplx<double>);
   int threads = ((c.n + 31) / 32) * 32;
-  set_dynamic_smem((const void*)k_self_inverse<float2>, smem);
-  k_self_inverse<float2><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(), c.n, c.nv, mu_c);
+  if (c.prec == PREC_F16) {
+    // the inverses feed FP16 operator images: Gauss-Jordan in FP32 (FP64 is slow on this GPU)
+    const size_t smem32 = (size_t)c.n * 2 * c.n * sizeof(cplx<float>);
+    set_dynamic_smem((const void*)k_self_inverse<float2, float>, smem32);
+    k_self_inverse<float2, float><<<ne, threads, smem32, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(),
+                                                               c.n, c.nv, mu_c);
+  } else {
+    set_dynamic_smem((const void*)k_self_inverse<float2, double>, smem);
+    k_self_inverse<float2, double><<<ne, threads, smem, st>>>(c.Dinv.as<float2>(), c.Dc.as<float2>(), c.even.as<int>(),
+                                                                c.n, c.nv, mu_c);
+  }
   CKL("self_inverse");
   if (c.prec == PREC_F16) build_inverse_images(c, st);
   c.inv_mu = mu_c;
