@@ -122,3 +122,19 @@ def test_oracle_estimate_bookkeeping():
     # each family scales with its own unit time only
     t2, _ = bench.oracle_estimate(dict(unit, galerkin=3.0), counts, V, Nc)
     assert t2 - t == 2.0 * counts["galerkin"]["launches"] * V
+
+
+def test_oracle_study_times_the_plain_method_on_4x4x4x4():
+    """bench.py --study oracle (direct timings of the oracle, no GPU): on the 4^4 parameter set the
+    operator build, one D(mu) application, one SAP cycle and the plain FP64 GMRES solve are timed,
+    and the solve reaches relative residual 1e-10."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--study", "oracle", "--lattices", "4x4x4x4"],
+                       capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["study"] == "oracle" and [row["lattice"] for row in out["rows"]] == ["4x4x4x4"]
+    row = out["rows"][0]
+    for k in ("operator_build_s", "apply_D_s", "sap_cycle_s", "gmres_solve_s"):
+        assert row[k] > 0, k
+    assert row["gmres_relres"] <= 1e-10 and row["sites"] == 256
