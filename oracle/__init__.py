@@ -1,9 +1,11 @@
 """Plain, slow FP64 CPU oracle for twisted-mass DD-alpha-AMG (arXiv:1610.02370).
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package:
-only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` use it.  It shares no code with the CUDA library; both sides only
-receive the same seeded inputs.
+only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s measurements
+around the product (the CPU-baseline timings: the ``cpu_baseline`` leg, the
+reference arm and ``--study oracle``; and the residual check of the timed
+solutions, after the timed region) use it.  It shares no code with the CUDA
+library; both sides only receive the same seeded inputs.
 
 Conventions (fixed here, used by every module of the oracle):
 
